@@ -1,0 +1,354 @@
+"""Benchmark of the C*-boundary Wilson-clover Dirac operator on GB300.
+
+Workload: physical lattice L = 48, T = 96 with C* boundaries in x, y, z,
+simulated as the doubled 96 x 96 x 48 x 48 lattice (21,233,664 sites);
+seeded SU(3) links exp(i 0.3 H), U(1) angles 0.3 * N(0,1), Gaussian source.
+One step = one application of D in FP32 (SU(3) links as two rows plus the
+U(1) angle, clover as two Hermitian 6x6 blocks per site) at charge qhat = 2,
+on native-layout buffers resident in HBM. The metric is Dw GB/s: the
+compulsory bytes of one application (688 B per site: spinor in 96 + out 96,
+links 4 x 48, angles 16, clover 288) divided by its time. The working set
+(14.6 GB per application) is far larger than L2, so no flush is needed.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of sites
+of the same workload (the oracle is a deliberately plain program; the ratio
+to it says nothing about kernel quality).
+
+Multi-GPU (torchrun, N > 1): independent replicas, one per GPU; the value is
+the bytes of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(T=96, L1=48, L2=48, L3=48, mask=0b1110, eps=0.3, sigma=0.3,
+                m0=0.1, csw=1.0, cswqed=1.0, qhat=2)
+BYTES_PER_SITE_FP32 = {True: 688, False: 672}   # qhat != 0 -> angles read
+BYTES_PER_SITE_FP64 = {True: 1568, False: 1536}
+METRIC = "Dw GB/s"
+FALLBACK_HBM = 6800.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_record(kernel_files):
+    """Per-launch DRAM traffic of the timed kernel from the committed ncu
+    summary, or None when the kernel source changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "dirac_fp32_q2_traffic.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p))
+    h = hashlib.sha256()
+    for f in kernel_files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if rec.get("source_sha256") != h.hexdigest():
+        return None
+    return rec
+
+
+def make_inputs(device):
+    import synth
+    w = WORKLOAD
+    su3 = synth.su3_field(w["T"], w["L1"], w["L2"], w["L3"], w["eps"], synth.SEED_GAUGE + 1,
+                          device=device)
+    ang = synth.u1_field(w["T"], w["L1"], w["L2"], w["L3"], w["sigma"], synth.SEED_GAUGE + 501,
+                         device=device)
+    N1 = 2 * w["L1"]
+    V = w["T"] * N1 * w["L2"] * w["L3"]
+    psi = synth.spinor_field(w["T"], N1, w["L2"], w["L3"], synth.SEED_SOURCE + 1).reshape(V, 4, 3)
+    return su3, ang, psi, V
+
+
+def oracle_sample_rate(su3_host, ang_host, psi_host, V, target_s=12.0):
+    """FP64 oracle on a sample of sites of the workload: (sites/s, sites, seconds)."""
+    import numpy as np
+
+    import oracle as O
+    w = WORKLOAD
+    lat = O.Lattice(w["T"], w["L1"], w["L2"], w["L3"], w["mask"])
+    op = O.Dirac(lat, O.GaugeField.from_physical(lat, su3_host, ang_host), w["m0"], w["csw"],
+                 w["cswqed"], w["qhat"])
+    rng = np.random.default_rng(7)
+    n = 2048
+    idx = rng.choice(V, size=n, replace=False)
+    t0 = time.perf_counter()
+    op.apply_at(psi_host, idx)
+    dt = time.perf_counter() - t0
+    n2 = int(min(200000, max(n, n * target_s / max(dt, 1e-3))))
+    idx = rng.choice(V, size=n2, replace=False)
+    t0 = time.perf_counter()
+    op.apply_at(psi_host, idx)
+    dt = time.perf_counter() - t0
+    return n2 / dt, n2, dt
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, sampled steps."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    su3, ang, psi, V = make_inputs(dev)
+    su3h, angh, psih = su3.cpu().numpy(), ang.cpu().numpy(), psi.numpy()
+    del su3, ang
+    w = WORKLOAD
+    lat = O.Lattice(w["T"], w["L1"], w["L2"], w["L3"], w["mask"])
+    op = O.Dirac(lat, O.GaugeField.from_physical(lat, su3h, angh), w["m0"], w["csw"],
+                 w["cswqed"], w["qhat"])
+    rng = np.random.default_rng(11)
+    S = 4096
+    samples = [rng.choice(V, size=S, replace=False) for _ in range(args.warmup + args.steps)]
+    for i in range(args.warmup):
+        op.apply_at(psih, samples[i])
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        op.apply_at(psih, samples[args.warmup + i])
+    dt = time.perf_counter() - t0
+    sites_s = S * args.steps / dt
+    b = BYTES_PER_SITE_FP64[True]
+    value = sites_s * b / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "Dw apply, doubled 96x96x48x48 C* lattice (L=48, T=96), qhat=2",
+                   "sample": f"{S} random sites per step, FP64 oracle",
+                   "bytes_per_site": b},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{S} random sites per step x {args.steps} steps "
+                                   f"({sites_s:.0f} sites/s)"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_1710_08839_gb300 import qxd
+
+    w = WORKLOAD
+    su3, ang, psi, V = make_inputs("cuda")
+    lat = qxd.Lattice(w["T"], w["L1"], w["L2"], w["L3"], w["mask"])
+    lat.set_gauge(su3, ang)
+    lat.set_params(w["m0"], w["csw"], w["cswqed"], w["qhat"])
+    lat.sw_build()
+    stream = torch.cuda.current_stream()
+
+    def native_pair(prec, dtype):
+        x = psi.to(dtype).cuda()
+        xn = torch.empty(lat.spinor_bytes(prec), dtype=torch.uint8, device="cuda")
+        lat.pack(xn, x, prec)
+        del x
+        return xn, torch.empty_like(xn)
+
+    def time_applies(prec, xn, yn, steps, warmup):
+        for _ in range(warmup):
+            lat.Dw(yn, xn, prec=prec, native=True)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            lat.Dw(yn, xn, prec=prec, native=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # headline: FP32, qhat = 2
+    xn, yn = native_pair(qxd.QXD_FP32, torch.complex64)
+    with ClockSampler(local) as clk:
+        ms = time_applies(qxd.QXD_FP32, xn, yn, args.steps, args.warmup)
+    clocks = clk.summary()
+    bps = BYTES_PER_SITE_FP32[True]
+    gbs_rank = bps * V / (ms * 1e-3) / 1e9
+    value = gbs_rank * ws
+    peak, peak_kind = _peaks()
+
+    variants = {}
+    if not args.no_variants:
+        vsteps = max(3, min(args.steps, 10))
+        lat.set_params(w["m0"], w["csw"], w["cswqed"], 0)
+        lat.sw_build()
+        ms0 = time_applies(qxd.QXD_FP32, xn, yn, vsteps, 3)
+        variants["fp32_q0"] = {"ms": ms0, "GB/s": BYTES_PER_SITE_FP32[False] * V / ms0 / 1e6,
+                               "bytes_per_site": BYTES_PER_SITE_FP32[False]}
+        lat.set_params(w["m0"], w["csw"], w["cswqed"], w["qhat"])
+        lat.sw_build()
+        del xn, yn
+        xd, yd = native_pair(qxd.QXD_FP64, torch.complex128)
+        ms64 = time_applies(qxd.QXD_FP64, xd, yd, max(3, min(args.steps, 5)), 3)
+        variants["fp64_q2"] = {"ms": ms64, "GB/s": BYTES_PER_SITE_FP64[True] * V / ms64 / 1e6,
+                               "bytes_per_site": BYTES_PER_SITE_FP64[True],
+                               "note": "FP64 Dw is bound by the FP64 ALUs, not HBM"}
+        del xd, yd
+
+    # end to end: host (pinned) lexicographic buffers through the C ABI
+    xh = psi.to(torch.complex64).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    e2e_steps = max(3, min(args.steps, 5))
+    lat.Dw(yh, xh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.Dw(yh, xh)
+    e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_val = bps * V / (e2e_ms * 1e-3) / 1e9 * ws
+    # read back one value of the result (the step's "metric")
+    _ = float(yh[0, 0, 0].real)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        su3h, angh = su3.cpu().numpy(), ang.cpu().numpy()
+        rate, n, dt = oracle_sample_rate(su3h, angh, psi.numpy(), V)
+        cpu = {"value": rate * BYTES_PER_SITE_FP64[True] / 1e9, "unit": "GB/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"FP64 oracle D at {n} random sites of the workload in {dt:.1f} s "
+                         f"({rate:.0f} sites/s, FP64 byte model 1568 B/site)"}
+
+    rec = _traffic_record(["paper_1710_08839_gb300/csrc/dirac.cu",
+                           "paper_1710_08839_gb300/csrc/dirac_common.cuh"])
+    traffic = rec["bytes_per_launch"] if rec else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "Dw apply FP32 (2-row SU(3) + U(1) angle), doubled 96x96x48x48 "
+                               "C* lattice (L=48, T=96), qhat=2, csw=cswqed=1",
+                   "sites": V, "bytes_per_site": bps, "l2": "inputs larger than L2 "
+                   f"({bps * V / 1e9:.1f} GB per step), no flush",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": gbs_rank, "peak": peak, "unit": "GB/s",
+                     "frac": gbs_rank / peak, "peak_source": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes": bps * V},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": V * 96,
+                "d2h_bytes_per_step": V * 96, "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "variants": variants,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

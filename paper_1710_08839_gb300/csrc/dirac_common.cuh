@@ -1,0 +1,240 @@
+// Device building blocks of the Dirac-operator kernels: native-layout loads
+// and stores, SU(3) products, spin projection and reconstruction, U(1)
+// phases and the clover-block product. Shared by the full-lattice, even-odd
+// and Schwarz-block kernels.
+#pragma once
+
+#include "qxd_internal.cuh"
+
+namespace qxd {
+
+constexpr int DW_THREADS = 256;
+
+template <typename R>
+struct Fields;
+
+template <>
+struct Fields<float> {
+    using vec = float4;
+    const float4* __restrict__ psi;
+    float4* __restrict__ out;
+    const float4* __restrict__ U;  // [4][3][V] two rows
+    const float4* __restrict__ A;  // [V] four angles
+    const float4* __restrict__ C;  // [18][V] clover (or inverse)
+};
+
+template <>
+struct Fields<double> {
+    using vec = double2;
+    const double2* __restrict__ psi;
+    double2* __restrict__ out;
+    const double2* __restrict__ U;  // [4][9][V]
+    const double* __restrict__ A;   // [4][V]
+    const double* __restrict__ C;   // [72][V]
+};
+
+// ---------------------------------------------------------------------------
+// spinors: v[3*spin + colour]
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_spinor(const float4* __restrict__ p, int V, int s, cplx<float> v[12]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        float4 t = p[(size_t)k * V + s];
+        v[2 * k] = mk(t.x, t.y);
+        v[2 * k + 1] = mk(t.z, t.w);
+    }
+}
+__device__ __forceinline__ void load_spinor(const double2* __restrict__ p, int V, int s, cplx<double> v[12]) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        double2 t = p[(size_t)k * V + s];
+        v[k] = mk(t.x, t.y);
+    }
+}
+__device__ __forceinline__ void store_spinor(float4* __restrict__ p, int V, int s, const cplx<float> v[12]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) p[(size_t)k * V + s] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
+}
+__device__ __forceinline__ void store_spinor(double2* __restrict__ p, int V, int s, const cplx<double> v[12]) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[(size_t)k * V + s] = make_double2(v[k].re, v[k].im);
+}
+
+// ---------------------------------------------------------------------------
+// links
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_link(const float4* __restrict__ U, int V, int mu, int s, cplx<float> u[3][3]) {
+    const float4 a = U[((size_t)mu * 3 + 0) * V + s];
+    const float4 b = U[((size_t)mu * 3 + 1) * V + s];
+    const float4 c = U[((size_t)mu * 3 + 2) * V + s];
+    u[0][0] = mk(a.x, a.y);
+    u[0][1] = mk(a.z, a.w);
+    u[0][2] = mk(b.x, b.y);
+    u[1][0] = mk(b.z, b.w);
+    u[1][1] = mk(c.x, c.y);
+    u[1][2] = mk(c.z, c.w);
+    // SU(3): row 2 = conj(row0 x row1)
+    u[2][0] = conj(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
+    u[2][1] = conj(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
+    u[2][2] = conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+}
+__device__ __forceinline__ void load_link(const double2* __restrict__ U, int V, int mu, int s, cplx<double> u[3][3]) {
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        double2 t = U[((size_t)mu * 9 + e) * V + s];
+        u[e / 3][e % 3] = mk(t.x, t.y);
+    }
+}
+
+__device__ __forceinline__ float load_angle(const float4* __restrict__ A, int V, int mu, int s) {
+    const float* a = reinterpret_cast<const float*>(A + s);
+    return a[mu];
+}
+__device__ __forceinline__ double load_angle(const double* __restrict__ A, int V, int mu, int s) {
+    return A[(size_t)mu * V + s];
+}
+__device__ __forceinline__ void load_angles4(const float4* __restrict__ A, int V, int s, float a[4]) {
+    float4 t = A[s];
+    a[0] = t.x;
+    a[1] = t.y;
+    a[2] = t.z;
+    a[3] = t.w;
+}
+__device__ __forceinline__ void load_angles4(const double* __restrict__ A, int V, int s, double a[4]) {
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) a[mu] = A[(size_t)mu * V + s];
+}
+
+__device__ __forceinline__ cplx<float> phase_of(float t) {
+    float sn, cs;
+    sincosf(t, &sn, &cs);
+    return mk(cs, sn);
+}
+__device__ __forceinline__ cplx<double> phase_of(double t) {
+    double sn, cs;
+    sincos(t, &sn, &cs);
+    return mk(cs, sn);
+}
+
+template <typename R>
+__device__ __forceinline__ void times3(cplx<R> ph, cplx<R> v[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = ph * v[c];
+}
+
+// g = u h
+template <typename R>
+__device__ __forceinline__ void su3_mul(const cplx<R> u[3][3], const cplx<R> h[3], cplx<R> g[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[a] = u[a][0] * h[0] + u[a][1] * h[1] + u[a][2] * h[2];
+}
+// g = u^+ h
+template <typename R>
+__device__ __forceinline__ void su3_dag_mul(const cplx<R> u[3][3], const cplx<R> h[3], cplx<R> g[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[a] = cmul(u[0][a], h[0]) + cmul(u[1][a], h[1]) + cmul(u[2][a], h[2]);
+}
+
+// ---------------------------------------------------------------------------
+// spin projection (1 - DIR g_mu) and its reconstruction, chiral basis
+// ---------------------------------------------------------------------------
+template <typename R, int MU, int DIR>
+__device__ __forceinline__ void project(const cplx<R> p[12], cplx<R> h0[3], cplx<R> h1[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cplx<R> a0 = p[c], a1 = p[3 + c], a2 = p[6 + c], a3 = p[9 + c];
+        if (MU == 0) {
+            h0[c] = DIR > 0 ? a0 + a2 : a0 - a2;
+            h1[c] = DIR > 0 ? a1 + a3 : a1 - a3;
+        } else if (MU == 1) {
+            h0[c] = DIR > 0 ? a0 + times_i(a3) : a0 - times_i(a3);
+            h1[c] = DIR > 0 ? a1 + times_i(a2) : a1 - times_i(a2);
+        } else if (MU == 2) {
+            h0[c] = DIR > 0 ? a0 + a3 : a0 - a3;
+            h1[c] = DIR > 0 ? a1 - a2 : a1 + a2;
+        } else {
+            h0[c] = DIR > 0 ? a0 + times_i(a2) : a0 - times_i(a2);
+            h1[c] = DIR > 0 ? a1 - times_i(a3) : a1 + times_i(a3);
+        }
+    }
+}
+
+template <typename R, int MU, int DIR>
+__device__ __forceinline__ void accumulate(cplx<R> acc[12], const cplx<R> g0[3], const cplx<R> g1[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[c] = acc[c] + g0[c];
+        acc[3 + c] = acc[3 + c] + g1[c];
+        if (MU == 0) {
+            acc[6 + c] = DIR > 0 ? acc[6 + c] + g0[c] : acc[6 + c] - g0[c];
+            acc[9 + c] = DIR > 0 ? acc[9 + c] + g1[c] : acc[9 + c] - g1[c];
+        } else if (MU == 1) {
+            acc[6 + c] = DIR > 0 ? acc[6 + c] + times_mi(g1[c]) : acc[6 + c] + times_i(g1[c]);
+            acc[9 + c] = DIR > 0 ? acc[9 + c] + times_mi(g0[c]) : acc[9 + c] + times_i(g0[c]);
+        } else if (MU == 2) {
+            acc[6 + c] = DIR > 0 ? acc[6 + c] - g1[c] : acc[6 + c] + g1[c];
+            acc[9 + c] = DIR > 0 ? acc[9 + c] + g0[c] : acc[9 + c] - g0[c];
+        } else {
+            acc[6 + c] = DIR > 0 ? acc[6 + c] + times_mi(g0[c]) : acc[6 + c] + times_i(g0[c]);
+            acc[9 + c] = DIR > 0 ? acc[9 + c] + times_i(g1[c]) : acc[9 + c] + times_mi(g1[c]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// clover blocks: y = M v, two Hermitian 6x6 blocks, packed (6 real diag,
+// 15 complex strictly-lower entries row major)
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void herm6_mul(const R d[6], const cplx<R> L[15], const cplx<R> v[6], cplx<R> y[6]) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) y[i] = d[i] * v[i];
+    int k = 0;
+#pragma unroll
+    for (int i = 1; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < i; ++j, ++k) {
+            y[i] = y[i] + L[k] * v[j];
+            y[j] = y[j] + cmul(L[k], v[i]);
+        }
+}
+
+__device__ __forceinline__ void clover_mul(const float4* __restrict__ C, int V, int s, const cplx<float> v[12],
+                                           cplx<float> w[12]) {
+#pragma unroll
+    for (int blk = 0; blk < 2; ++blk) {
+        float r[36];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            float4 t = C[(size_t)(9 * blk + q) * V + s];
+            r[4 * q] = t.x;
+            r[4 * q + 1] = t.y;
+            r[4 * q + 2] = t.z;
+            r[4 * q + 3] = t.w;
+        }
+        float d[6];
+        cplx<float> L[15];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) d[i] = r[i];
+#pragma unroll
+        for (int k = 0; k < 15; ++k) L[k] = mk(r[6 + 2 * k], r[7 + 2 * k]);
+        herm6_mul(d, L, v + 6 * blk, w + 6 * blk);
+    }
+}
+
+__device__ __forceinline__ void clover_mul(const double* __restrict__ C, int V, int s, const cplx<double> v[12],
+                                           cplx<double> w[12]) {
+#pragma unroll
+    for (int blk = 0; blk < 2; ++blk) {
+        double d[6];
+        cplx<double> L[15];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) d[i] = C[(size_t)(36 * blk + i) * V + s];
+#pragma unroll
+        for (int k = 0; k < 15; ++k)
+            L[k] = mk(C[(size_t)(36 * blk + 6 + 2 * k) * V + s], C[(size_t)(36 * blk + 7 + 2 * k) * V + s]);
+        herm6_mul(d, L, v + 6 * blk, w + 6 * blk);
+    }
+}
+
+}  // namespace qxd

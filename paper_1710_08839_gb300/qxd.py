@@ -1,0 +1,240 @@
+"""Thin Python binding of the qxd C ABI (include/qxd.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libqxd.so. Functions carry the C names (``qxd_lattice_create``,
+``qxd_set_gauge``, ...) and take raw pointers (ints) and sizes; the
+``Lattice`` class wraps them for torch tensors. There is no CPU fallback:
+if libqxd.so has not been built, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+QXD_OK = 0
+QXD_ERR_ARG = -1
+QXD_ERR_OOM = -2
+QXD_ERR_CUDA = -3
+QXD_ERR_NOT_ADMISSIBLE = -4
+QXD_ERR_SW_SINGULAR = -5
+QXD_ERR_NOT_CONVERGED = -6
+QXD_ERR_NUMERIC = -7
+QXD_ERR_STATE = -8
+QXD_ERR_TIMEOUT = -9
+
+QXD_FP64 = 0x0
+QXD_FP32 = 0x1
+QXD_DEVICE = 0x0
+QXD_HOST = 0x10
+QXD_LAYOUT_LEX = 0x0
+QXD_LAYOUT_NATIVE = 0x100
+QXD_GAUGE_PHYSICAL_HALF = 0x0
+QXD_GAUGE_EXTENDED_CHECKED = 0x1
+QXD_GAUGE_EXTENDED_UNCHECKED = 0x2
+QXD_GAUGE_HOST = 0x10
+
+_STATUS_NAMES = {
+    0: "QXD_OK", -1: "QXD_ERR_ARG", -2: "QXD_ERR_OOM", -3: "QXD_ERR_CUDA",
+    -4: "QXD_ERR_NOT_ADMISSIBLE", -5: "QXD_ERR_SW_SINGULAR", -6: "QXD_ERR_NOT_CONVERGED",
+    -7: "QXD_ERR_NUMERIC", -8: "QXD_ERR_STATE", -9: "QXD_ERR_TIMEOUT",
+}
+
+
+class QxdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        self.code = code
+        super().__init__(f"{_STATUS_NAMES.get(code, code)}: {msg}")
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+
+# name -> (restype, argtypes); mirrors include/qxd.h
+SIGNATURES = {
+    "qxd_lattice_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, ctypes.c_uint, _vp]),
+    "qxd_lattice_destroy": (_i, [_vp]),
+    "qxd_lattice_dims": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_longlong)]),
+    "qxd_set_gauge": (_i, [_vp, _vp, _vp, _i]),
+    "qxd_set_params": (_i, [_vp, _d, _d, _d, _i]),
+    "qxd_sw_build": (_i, [_vp]),
+    "qxd_Dw": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "qxd_spinor_bytes": (ctypes.c_size_t, [_vp, _i]),
+    "qxd_spinor_pack": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "qxd_spinor_unpack": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "qxd_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded libqxd.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libqxd.so not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def check(rc: int) -> int:
+    if rc != QXD_OK:
+        raise QxdError(rc, lib().qxd_last_error().decode())
+    return rc
+
+
+def _call(name, *args):
+    return getattr(lib(), name)(*args)
+
+
+# C-named entry points (raw pointers as ints) ------------------------------
+
+def qxd_lattice_create(T, L1, L2, L3, cstar_mask, stream=0) -> int:
+    h = _vp()
+    check(_call("qxd_lattice_create", ctypes.byref(h), T, L1, L2, L3, cstar_mask, stream))
+    return h.value
+
+
+def qxd_lattice_destroy(lat) -> int:
+    return check(_call("qxd_lattice_destroy", lat))
+
+
+def qxd_set_gauge(lat, su3_ptr, u1_ptr, flags) -> int:
+    return check(_call("qxd_set_gauge", lat, su3_ptr, u1_ptr, flags))
+
+
+def qxd_set_params(lat, m0, csw, cswqed, qhat) -> int:
+    return check(_call("qxd_set_params", lat, m0, csw, cswqed, int(qhat)))
+
+
+def qxd_sw_build(lat) -> int:
+    return check(_call("qxd_sw_build", lat))
+
+
+def qxd_Dw(lat, out_ptr, in_ptr, flags, stream=0) -> int:
+    return check(_call("qxd_Dw", lat, out_ptr, in_ptr, flags, stream))
+
+
+def qxd_spinor_bytes(lat, prec) -> int:
+    return _call("qxd_spinor_bytes", lat, prec)
+
+
+def qxd_spinor_pack(lat, nat_ptr, lex_ptr, prec, stream=0) -> int:
+    return check(_call("qxd_spinor_pack", lat, nat_ptr, lex_ptr, prec, stream))
+
+
+def qxd_spinor_unpack(lat, lex_ptr, nat_ptr, prec, stream=0) -> int:
+    return check(_call("qxd_spinor_unpack", lat, lex_ptr, nat_ptr, prec, stream))
+
+
+def qxd_last_error() -> str:
+    return lib().qxd_last_error().decode()
+
+
+# torch convenience wrapper -------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _real_ptr(t):
+    """Pointer of a contiguous tensor (complex tensors through their real view)."""
+    torch = _torch()
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr(), (t.device.type == "cpu"), t
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+        return 0
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Lattice:
+    """One lattice (gauge field, parameters, clover term) on the current GPU.
+
+    Spinors are torch tensors: lexicographic layout (V, 4, 3) complex128 for
+    FP64 or complex64 for FP32, on the GPU (or on the host, which makes the
+    call copy through device scratch), or native-layout device buffers of
+    ``spinor_bytes(prec)`` bytes.
+    """
+
+    def __init__(self, T, L1, L2, L3, cstar_mask=0b1110, stream=None):
+        self.T, self.L1, self.L2, self.L3 = T, L1, L2, L3
+        self.cstar_mask = cstar_mask
+        self.handle = qxd_lattice_create(T, L1, L2, L3, cstar_mask, _stream_ptr(stream))
+        N = (_i * 4)()
+        V = ctypes.c_longlong()
+        check(_call("qxd_lattice_dims", self.handle, N, ctypes.byref(V)))
+        self.N = tuple(N)
+        self.V = V.value
+
+    def close(self):
+        if self.handle:
+            qxd_lattice_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_gauge(self, su3, angle, flags=QXD_GAUGE_PHYSICAL_HALF):
+        torch = _torch()
+        su3 = su3.contiguous()
+        angle = angle.to(torch.float64).contiguous()
+        if su3.dtype != torch.complex128 or su3.shape[-3:] != (4, 3, 3):
+            raise ValueError("su3 must be complex128 (..., 4, 3, 3)")
+        if su3.device != angle.device:
+            raise ValueError("su3 and angle must be on the same device")
+        host = su3.device.type == "cpu"
+        qxd_set_gauge(self.handle, su3.data_ptr(), angle.data_ptr(),
+                      flags | (QXD_GAUGE_HOST if host else 0))
+
+    def set_params(self, m0, csw, cswqed, qhat):
+        qxd_set_params(self.handle, m0, csw, cswqed, qhat)
+        self.qhat = int(qhat)
+
+    def sw_build(self):
+        qxd_sw_build(self.handle)
+
+    def spinor_bytes(self, prec):
+        return qxd_spinor_bytes(self.handle, prec)
+
+    def Dw(self, out, inp, prec=None, native=False, stream=None):
+        torch = _torch()
+        if prec is None:
+            prec = QXD_FP32 if inp.dtype in (torch.complex64, torch.float32) else QXD_FP64
+        flags = prec
+        if native:
+            flags |= QXD_LAYOUT_NATIVE
+        if inp.device.type == "cpu":
+            flags |= QXD_HOST
+            if out.device.type != "cpu":
+                raise ValueError("host input needs host output")
+        if not (inp.is_contiguous() and out.is_contiguous()):
+            raise ValueError("spinors must be contiguous")
+        qxd_Dw(self.handle, out.data_ptr(), inp.data_ptr(), flags, _stream_ptr(stream))
+        return out
+
+    def pack(self, native_out, lex_in, prec, stream=None):
+        qxd_spinor_pack(self.handle, native_out.data_ptr(), lex_in.data_ptr(), prec, _stream_ptr(stream))
+        return native_out
+
+    def unpack(self, lex_out, native_in, prec, stream=None):
+        qxd_spinor_unpack(self.handle, lex_out.data_ptr(), native_in.data_ptr(), prec, _stream_ptr(stream))
+        return lex_out
