@@ -31,8 +31,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(T=96, L1=48, L2=48, L3=48, mask=0b1110, eps=0.3, sigma=0.3,
-                m0=0.1, csw=1.0, cswqed=1.0, qhat=2)
+WORKLOADS = {
+    # the throughput workload: physical L = 48, T = 96, doubled 96x96x48x48
+    "full": dict(T=96, L1=48, L2=48, L3=48, mask=0b1110, eps=0.3, sigma=0.3,
+                 m0=0.1, csw=1.0, cswqed=1.0, qhat=2),
+    # a smaller case of the same kernel for profiling (48x48x24x24, 0.9 GB/step)
+    "medium": dict(T=48, L1=24, L2=24, L3=24, mask=0b1110, eps=0.3, sigma=0.3,
+                   m0=0.1, csw=1.0, cswqed=1.0, qhat=2),
+}
+WORKLOAD = WORKLOADS["full"]
 BYTES_PER_SITE_FP32 = {True: 688, False: 672}   # qhat != 0 -> angles read
 BYTES_PER_SITE_FP64 = {True: 1568, False: 1536}
 METRIC = "Dw GB/s"
@@ -57,7 +64,7 @@ def _dist():
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -70,7 +77,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -87,13 +94,23 @@ class ClockSampler:
             out = ""
         self.lines = [l for l in out.splitlines() if l.strip()]
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
+        """Median SM clock and active throttle reasons of the samples taken
+        between wall-clock times t0 and t1 (all samples if not given)."""
+        import datetime
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for l in self.lines:
             f = [x.strip() for x in l.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            if t0 is not None and ts is not None and not (t0 - 0.15 <= ts <= t1 + 0.15):
+                continue
+            f = f[1:]
             try:
                 sm.append(float(f[1]))
                 smax = float(f[2])
@@ -124,9 +141,9 @@ def _traffic_record(kernel_files):
     return rec
 
 
-def make_inputs(device):
+def make_inputs(device, w=None):
     import synth
-    w = WORKLOAD
+    w = w or WORKLOAD
     su3 = synth.su3_field(w["T"], w["L1"], w["L2"], w["L3"], w["eps"], synth.SEED_GAUGE + 1,
                           device=device)
     ang = synth.u1_field(w["T"], w["L1"], w["L2"], w["L3"], w["sigma"], synth.SEED_GAUGE + 501,
@@ -137,12 +154,11 @@ def make_inputs(device):
     return su3, ang, psi, V
 
 
-def oracle_sample_rate(su3_host, ang_host, psi_host, V, target_s=12.0):
+def oracle_sample_rate(su3_host, ang_host, psi_host, V, w, target_s=12.0):
     """FP64 oracle on a sample of sites of the workload: (sites/s, sites, seconds)."""
     import numpy as np
 
     import oracle as O
-    w = WORKLOAD
     lat = O.Lattice(w["T"], w["L1"], w["L2"], w["L3"], w["mask"])
     op = O.Dirac(lat, O.GaugeField.from_physical(lat, su3_host, ang_host), w["m0"], w["csw"],
                  w["cswqed"], w["qhat"])
@@ -208,11 +224,13 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -230,8 +248,8 @@ def main():
     ge.build()
     from paper_1710_08839_gb300 import qxd
 
-    w = WORKLOAD
-    su3, ang, psi, V = make_inputs("cuda")
+    w = WORKLOADS[args.workload]
+    su3, ang, psi, V = make_inputs("cuda", w)
     lat = qxd.Lattice(w["T"], w["L1"], w["L2"], w["L3"], w["mask"])
     lat.set_gauge(su3, ang)
     lat.set_params(w["m0"], w["csw"], w["cswqed"], w["qhat"])
@@ -245,19 +263,28 @@ def main():
         del x
         return xn, torch.empty_like(xn)
 
-    def time_applies(prec, xn, yn, steps, warmup):
-        for _ in range(warmup):
+    window = {}
+
+    def time_applies(prec, xn, yn, steps, warmup, min_warm_s=0.0):
+        t_w = time.perf_counter()
+        n = 0
+        while n < warmup or time.perf_counter() - t_w < min_warm_s:
             lat.Dw(yn, xn, prec=prec, native=True)
+            n += 1
+            if n % 50 == 0:
+                torch.cuda.synchronize()
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        window["t0"] = time.time()
         e0.record(stream)
         for _ in range(steps):
             lat.Dw(yn, xn, prec=prec, native=True)
         e1.record(stream)
         torch.cuda.synchronize()
+        window["t1"] = time.time()
         ms = e0.elapsed_time(e1) / steps
         if ws > 1:
             t = torch.tensor([ms], device="cuda")
@@ -268,8 +295,9 @@ def main():
     # headline: FP32, qhat = 2
     xn, yn = native_pair(qxd.QXD_FP32, torch.complex64)
     with ClockSampler(local) as clk:
-        ms = time_applies(qxd.QXD_FP32, xn, yn, args.steps, args.warmup)
-    clocks = clk.summary()
+        # warm up for >= 1 s so the sampler is running when the timed region starts
+        ms = time_applies(qxd.QXD_FP32, xn, yn, args.steps, args.warmup, min_warm_s=1.0)
+    clocks = clk.summary(window["t0"], window["t1"])
     bps = BYTES_PER_SITE_FP32[True]
     gbs_rank = bps * V / (ms * 1e-3) / 1e9
     value = gbs_rank * ws
@@ -293,28 +321,33 @@ def main():
                                "note": "FP64 Dw is bound by the FP64 ALUs, not HBM"}
         del xd, yd
 
-    # end to end: host (pinned) lexicographic buffers through the C ABI
-    xh = psi.to(torch.complex64).pin_memory()
-    yh = torch.empty_like(xh).pin_memory()
-    e2e_steps = max(3, min(args.steps, 5))
-    lat.Dw(yh, xh)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    # end to end: host (pinned) lexicographic buffers through the C ABI; the
+    # call copies the input in, packs, applies D, unpacks and copies the
+    # result out, then synchronises.
+    e2e = None
+    if not args.no_e2e:
+        xh = psi.to(torch.complex64).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        e2e_steps = max(3, min(args.steps, 5))
         lat.Dw(yh, xh)
-    e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_val = bps * V / (e2e_ms * 1e-3) / 1e9 * ws
-    # read back one value of the result (the step's "metric")
-    _ = float(yh[0, 0, 0].real)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            lat.Dw(yh, xh)
+        e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
+        if ws > 1:
+            t = torch.tensor([e2e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        _ = float(yh[0, 0, 0].real)  # the step's result is on the host
+        e2e = {"value": bps * V / (e2e_ms * 1e-3) / 1e9 * ws, "unit": "GB/s",
+               "h2d_bytes_per_step": V * 96, "d2h_bytes_per_step": V * 96, "ms_per_step": e2e_ms}
+        del xh, yh
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         su3h, angh = su3.cpu().numpy(), ang.cpu().numpy()
-        rate, n, dt = oracle_sample_rate(su3h, angh, psi.numpy(), V)
+        rate, n, dt = oracle_sample_rate(su3h, angh, psi.numpy(), V, w)
         cpu = {"value": rate * BYTES_PER_SITE_FP64[True] / 1e9, "unit": "GB/s", "cores": 1,
                "kind": "oracle",
                "sample": f"FP64 oracle D at {n} random sites of the workload in {dt:.1f} s "
@@ -327,8 +360,9 @@ def main():
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "Dw apply FP32 (2-row SU(3) + U(1) angle), doubled 96x96x48x48 "
-                               "C* lattice (L=48, T=96), qhat=2, csw=cswqed=1",
+        "config": {"workload": "Dw apply FP32 (2-row SU(3) + U(1) angle), doubled "
+                               f"{w['T']}x{2 * w['L1']}x{w['L2']}x{w['L3']} C* lattice "
+                               f"(L={w['L1']}, T={w['T']}), qhat={w['qhat']}, csw=cswqed=1",
                    "sites": V, "bytes_per_site": bps, "l2": "inputs larger than L2 "
                    f"({bps * V / 1e9:.1f} GB per step), no flush",
                    "parallelism": f"replicas x{ws}"},
@@ -336,8 +370,7 @@ def main():
                      "frac": gbs_rank / peak, "peak_source": peak_kind, "traffic": traffic,
                      "algorithmic_bytes": bps * V},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": V * 96,
-                "d2h_bytes_per_step": V * 96, "ms_per_step": e2e_ms},
+        "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,
         "variants": variants,

@@ -142,6 +142,90 @@ int qxd_sw_build(qxd_lattice* lat);
  */
 int qxd_Dw(qxd_lattice* lat, void* out, const void* in, int flags, void* stream);
 
+/*
+ * Even-odd form (Sec. 2.4, Eqs. (29)-(30)). Sites are even when
+ * x0 + x1 + x2 + x3 is even. With D = M + H (M site-diagonal, H the hopping
+ * term, which connects only opposite parities):
+ *   qxd_Dhat:            out_e = D_hat in_e = (M_ee - H_eo M_oo^-1 H_oe) in_e
+ *   qxd_eo_prepare:      out_e = b_e - H_eo M_oo^-1 b_o   (source of D_hat x_e = out_e)
+ *   qxd_eo_reconstruct:  x_o   = M_oo^-1 (b_o - H_oe x_e) (x_e read from x, x_o written)
+ * All buffers are full-lattice spinor fields (flags as for qxd_Dw, device
+ * memory only); Dhat and prepare read the even sites of their input and
+ * write zeros on the odd sites of their output. Needs qxd_sw_build.
+ */
+int qxd_Dhat(qxd_lattice* lat, void* out, const void* in, int flags, void* stream);
+int qxd_eo_prepare(qxd_lattice* lat, void* out, const void* b, int flags, void* stream);
+int qxd_eo_reconstruct(qxd_lattice* lat, void* x, const void* b, int flags, void* stream);
+
+/*
+ * Schwarz alternating procedure (the preconditioner of the GCR solver; the
+ * paper names it, Sec. 1-2, without giving it): out = SAP(in), ncy cycles of
+ * the multiplicative Schwarz method on 4^4 blocks coloured by the parity of
+ * the block coordinates (blocks of colour 0, then colour 1); per block the
+ * residual in - D out is computed over the whole lattice and out += the
+ * result of nmr minimal-residual steps on the even-odd form of D restricted
+ * to the block (hops leaving the block dropped). Starts from out = 0.
+ * flags: precision and layout as for qxd_Dw, device buffers only. The
+ * lattice needs every extent a multiple of 8 and, with C* boundaries,
+ * L1 a multiple of 4 with L_k/4 + L1/4 even (else QXD_ERR_ARG).
+ */
+int qxd_sap(qxd_lattice* lat, void* out, const void* in, int ncy, int nmr, int flags, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Solver: D x = b to a true FP64 relative residual |b - D x| / |b| <= tol.
+ * Flexible GCR (the paper names GCR with SAP preconditioning, Sec. 1-2, but
+ * does not specify either): Krylov directions phi_k = P(r_k) from the
+ * preconditioner P, chi_k = A phi_k made orthonormal by Gram-Schmidt with
+ * FP64-accumulated inner products, x updated in FP64 at each restart,
+ * where the residual is recomputed as b - D x in FP64 (reliable update; also
+ * triggered when the inner residual falls below delta times the last true one).
+ * system QXD_SOLVE_FULL: GCR on D over the whole lattice.
+ * system QXD_SOLVE_EO:   GCR on D_hat for x_e, then x_o by reconstruction.
+ * precond QXD_PRECOND_SAP: Schwarz alternating procedure on 4^4 blocks
+ * (full system only; inner_prec FP32 or FP64).
+ * ------------------------------------------------------------------------- */
+#define QXD_PRECOND_NONE 0
+#define QXD_PRECOND_SAP 1
+#define QXD_SOLVE_FULL 0
+#define QXD_SOLVE_EO 1
+
+typedef struct {
+    double tol;       /* target true FP64 relative residual                          */
+    int max_iter;     /* limit on Krylov steps over all restarts                     */
+    int nkv;          /* Krylov vectors kept before a restart, 1..16                 */
+    int precond;      /* QXD_PRECOND_NONE | QXD_PRECOND_SAP                          */
+    int system;       /* QXD_SOLVE_FULL | QXD_SOLVE_EO                               */
+    int inner_prec;   /* QXD_FP64 | QXD_FP32: Krylov vectors, inner D, preconditioner */
+    int sap_ncy;      /* SAP cycles per preconditioner call                          */
+    int sap_nmr;      /* minimal-residual steps per block solve                      */
+    double delta;     /* reliable update when |r_inner| < delta |r_true| (0: off)    */
+    int flags;        /* x and b: QXD_DEVICE | QXD_HOST, QXD_LAYOUT_LEX | _NATIVE     */
+} qxd_solver_params;
+
+typedef struct {
+    int status;            /* QXD_OK, QXD_ERR_NOT_CONVERGED, QXD_ERR_NUMERIC        */
+    int iterations;        /* Krylov steps                                          */
+    int restarts;          /* true-residual recomputations (reliable updates)       */
+    double true_relres;    /* |b - D x| / |b| in FP64 at return                     */
+    double time_ms;        /* wall time of the call                                 */
+    int dw64_calls;        /* FP64 applications of D (or D_hat)                     */
+    int inner_calls;       /* applications of the inner operator                    */
+} qxd_solve_info;
+
+/* Defaults: tol 1e-10, max_iter 2000, nkv 16, no preconditioner, full system,
+ * FP64, ncy 5, nmr 5, delta 1e-4, device lexicographic buffers. */
+void qxd_solver_defaults(qxd_solver_params* p);
+
+/*
+ * Solve D x = b (FP64 fields, layout and location by params->flags; x is
+ * output only, the initial guess is zero). info may be NULL. Returns QXD_OK,
+ * QXD_ERR_NOT_CONVERGED (x and info still written), QXD_ERR_NUMERIC, or an
+ * argument/state error. Work vectors are allocated on the first call and
+ * kept with the lattice. Synchronises the stream.
+ */
+int qxd_solve(qxd_lattice* lat, void* x, const void* b, const qxd_solver_params* params,
+              qxd_solve_info* info, void* stream);
+
 /* Bytes of one spinor field in the native layout for precision `prec`. */
 size_t qxd_spinor_bytes(const qxd_lattice* lat, int prec);
 

@@ -42,14 +42,14 @@ static int dalloc(T** p, size_t n, const char* what) {
 }
 
 static void free_all(qxd_lattice* L) {
-    void* ptrs[] = {L->U64, L->U32, L->A64, L->A32, L->ftens, L->C64, L->C32,
+    void* ptrs[] = {L->U64, L->U32, L->A64, L->Z64, L->A32, L->ftens, L->C64, L->C32,
                     L->Cinv64, L->Cinv32, L->d_status, L->scratch_in, L->scratch_out,
                     L->scratch_lex};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
 
-static int ensure_scratch(qxd_lattice* L) {
+int ensure_scratch(qxd_lattice* L) {
     if (L->scratch_in) return QXD_OK;
     size_t nat = (size_t)L->g.V * SPINOR_D2 * sizeof(double2);
     int rc;
@@ -112,6 +112,7 @@ int qxd_lattice_create(qxd_lattice** out, int T, int L1, int L2, int L3, unsigne
     if ((rc = dalloc(&lat->U64, 4 * 9 * v, "cudaMalloc(U64)")) ||
         (rc = dalloc(&lat->U32, 4 * 3 * v, "cudaMalloc(U32)")) ||
         (rc = dalloc(&lat->A64, 4 * v, "cudaMalloc(A64)")) ||
+        (rc = dalloc(&lat->Z64, 4 * v, "cudaMalloc(Z64)")) ||
         (rc = dalloc(&lat->A32, v, "cudaMalloc(A32)")) ||
         (rc = dalloc(&lat->ftens, FTENS_REALS * v, "cudaMalloc(ftens)")) ||
         (rc = dalloc(&lat->C64, CLOVER_REALS * v, "cudaMalloc(C64)")) ||
@@ -130,6 +131,7 @@ int qxd_lattice_create(qxd_lattice** out, int T, int L1, int L2, int L3, unsigne
 int qxd_lattice_destroy(qxd_lattice* lat) {
     if (!lat) return QXD_OK;
     cudaStreamSynchronize(lat->stream);
+    release_solver(lat);
     free_all(lat);
     delete lat;
     return QXD_OK;

@@ -1,0 +1,315 @@
+// Vector kernels of the Krylov solvers (see blas.cuh).
+#include "blas.cuh"
+
+namespace qxd {
+
+namespace {
+
+__device__ __forceinline__ double2 ld(const float2* p, size_t i) {
+    float2 v = p[i];
+    return make_double2(v.x, v.y);
+}
+__device__ __forceinline__ double2 ld(const double2* p, size_t i) { return p[i]; }
+__device__ __forceinline__ void st_(float2* p, size_t i, double2 v) { p[i] = make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ void st_(double2* p, size_t i, double2 v) { p[i] = v; }
+
+// block-wide sum of NC values per thread into partials[blockIdx.x][0..NC)
+template <int NC>
+__device__ __forceinline__ void block_reduce_store(double v[NC], int nc, double* __restrict__ partials) {
+    __shared__ double sh[RED_THREADS / 32][2 * BLAS_KMAX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        if (c >= nc) break;
+        double x = v[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[warp][c] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+        double x = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) x += sh[w][threadIdx.x];
+        partials[(size_t)blockIdx.x * 2 * BLAS_KMAX + threadIdx.x] = x;
+    }
+}
+
+__global__ void k_reduce_final(const double* __restrict__ partials, int nc, double* __restrict__ res) {
+    const int c = threadIdx.x;
+    if (c >= nc) return;
+    double x = 0.0;
+    for (int b = 0; b < RED_BLOCKS; ++b) x += partials[(size_t)b * 2 * BLAS_KMAX + c];
+    res[c] = x;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_mdot(size_t n, int k, VecList<T> xs, const T* __restrict__ y,
+                                                      double* __restrict__ partials) {
+    double acc[2 * BLAS_KMAX];
+#pragma unroll
+    for (int c = 0; c < 2 * BLAS_KMAX; ++c) acc[c] = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 b = ld(y, i);
+#pragma unroll
+        for (int j = 0; j < BLAS_KMAX; ++j) {
+            if (j >= k) break;
+            const double2 a = ld(xs.p[j], i);
+            acc[2 * j] += a.x * b.x + a.y * b.y;
+            acc[2 * j + 1] += a.x * b.y - a.y * b.x;
+        }
+    }
+    block_reduce_store<2 * BLAS_KMAX>(acc, 2 * k, partials);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_norm2(size_t n, const T* __restrict__ x,
+                                                       double* __restrict__ partials) {
+    double acc[1] = {0.0};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 a = ld(x, i);
+        acc[0] += a.x * a.x + a.y * a.y;
+    }
+    block_reduce_store<1>(acc, 1, partials);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_maxpy_norm(size_t n, int k, CoefList c, VecList<T> xs,
+                                                            T* __restrict__ y, double* __restrict__ partials) {
+    double acc[1] = {0.0};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double2 b = ld(y, i);
+#pragma unroll
+        for (int j = 0; j < BLAS_KMAX; ++j) {
+            if (j >= k) break;
+            const double2 a = ld(xs.p[j], i);
+            b.x -= c.re[j] * a.x - c.im[j] * a.y;
+            b.y -= c.re[j] * a.y + c.im[j] * a.x;
+        }
+        st_(y, i, b);
+        const double2 r = ld(y, i);  // norm of the stored (rounded) vector
+        acc[0] += r.x * r.x + r.y * r.y;
+    }
+    block_reduce_store<1>(acc, 1, partials);
+}
+
+template <typename T>
+__global__ void k_caxpy(size_t n, double cre, double cim, const T* __restrict__ x, T* __restrict__ y) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 a = ld(x, i);
+        double2 b = ld(y, i);
+        b.x -= cre * a.x - cim * a.y;
+        b.y -= cre * a.y + cim * a.x;
+        st_(y, i, b);
+    }
+}
+
+template <typename T>
+__global__ void k_scale(size_t n, double s, T* __restrict__ x) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double2 a = ld(x, i);
+        a.x *= s;
+        a.y *= s;
+        st_(x, i, a);
+    }
+}
+
+// Native spinor layouts differ between precisions: FP64 keeps component c
+// (0..11) of site s at double2 index c * S + s, FP32 keeps it at float2
+// index (c / 2) * 2S + 2s + c % 2 (two components per float4). S is the
+// number of sites of the array (V, or V/2 for a half-lattice field).
+__device__ __forceinline__ size_t f32_index(size_t S, size_t c, size_t s) { return (c >> 1) * 2 * S + 2 * s + (c & 1); }
+
+__global__ void k_update_x_native32(size_t S, int k, CoefList c, VecList<float2> vs, double2* __restrict__ x) {
+    for (size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int comp = 0; comp < 12; ++comp) {
+            double2 b = x[comp * S + s];
+            const size_t i32 = f32_index(S, comp, s);
+            for (int j = 0; j < k; ++j) {
+                const float2 a = vs.p[j][i32];
+                b.x += c.re[j] * a.x - c.im[j] * a.y;
+                b.y += c.re[j] * a.y + c.im[j] * a.x;
+            }
+            x[comp * S + s] = b;
+        }
+    }
+}
+
+__global__ void k_d2f_native(size_t S, const double2* __restrict__ in, float2* __restrict__ out) {
+    for (size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int comp = 0; comp < 12; ++comp) {
+            const double2 v = in[comp * S + s];
+            out[f32_index(S, comp, s)] = make_float2((float)v.x, (float)v.y);
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_update_x(size_t n, int k, CoefList c, VecList<T> vs, double2* __restrict__ x) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double2 b = x[i];
+#pragma unroll
+        for (int j = 0; j < BLAS_KMAX; ++j) {
+            if (j >= k) break;
+            const double2 a = ld(vs.p[j], i);
+            b.x += c.re[j] * a.x - c.im[j] * a.y;
+            b.y += c.re[j] * a.y + c.im[j] * a.x;
+        }
+        x[i] = b;
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_sub_norm(size_t n, const double2* __restrict__ b,
+                                                          const double2* __restrict__ t, double2* __restrict__ r,
+                                                          double* __restrict__ partials) {
+    double acc[1] = {0.0};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 v = make_double2(b[i].x - t[i].x, b[i].y - t[i].y);
+        r[i] = v;
+        acc[0] += v.x * v.x + v.y * v.y;
+    }
+    block_reduce_store<1>(acc, 1, partials);
+}
+
+__global__ void k_d2f(size_t n, const double2* __restrict__ in, float2* __restrict__ out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+__global__ void k_f2d(size_t n, const float2* __restrict__ in, double2* __restrict__ out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = make_double2(in[i].x, in[i].y);
+}
+
+int finish(Reducer& red, int nc, cudaStream_t st) {
+    k_reduce_final<<<1, 2 * BLAS_KMAX, 0, st>>>(red.partials, nc, red.d_res);
+    QXD_LAUNCHED("k_reduce_final");
+    QXD_CUDA(cudaMemcpyAsync(red.h_res, red.d_res, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QXD_CUDA(cudaStreamSynchronize(st));
+    return QXD_OK;
+}
+
+inline int ew_blocks(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (int)(b < 4 * 152 * 4 ? b : 4 * 152 * 4);
+}
+
+}  // namespace
+
+int Reducer::init() {
+    if (partials) return QXD_OK;
+    QXD_CUDA(cudaMalloc(&partials, sizeof(double) * RED_BLOCKS * 2 * BLAS_KMAX));
+    QXD_CUDA(cudaMalloc(&d_res, sizeof(double) * 2 * BLAS_KMAX));
+    QXD_CUDA(cudaMallocHost(&h_res, sizeof(double) * 2 * BLAS_KMAX));
+    return QXD_OK;
+}
+
+void Reducer::release() {
+    if (partials) cudaFree(partials);
+    if (d_res) cudaFree(d_res);
+    if (h_res) cudaFreeHost(h_res);
+    partials = d_res = h_res = nullptr;
+}
+
+template <typename T>
+int blas_mdot(Reducer& red, size_t n, int k, const VecList<T>& xs, const T* y, cd* out, cudaStream_t st) {
+    if (k <= 0) return QXD_OK;
+    k_mdot<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, xs, y, red.partials);
+    QXD_LAUNCHED("k_mdot");
+    int rc = finish(red, 2 * k, st);
+    if (rc) return rc;
+    for (int j = 0; j < k; ++j) out[j] = cd(red.h_res[2 * j], red.h_res[2 * j + 1]);
+    return QXD_OK;
+}
+
+template <typename T>
+int blas_norm2(Reducer& red, size_t n, const T* x, double* out, cudaStream_t st) {
+    k_norm2<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, x, red.partials);
+    QXD_LAUNCHED("k_norm2");
+    int rc = finish(red, 1, st);
+    if (rc) return rc;
+    *out = red.h_res[0];
+    return QXD_OK;
+}
+
+template <typename T>
+int blas_maxpy_norm(Reducer& red, size_t n, int k, const CoefList& c, const VecList<T>& xs, T* y, double* nrm2,
+                    cudaStream_t st) {
+    k_maxpy_norm<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, c, xs, y, red.partials);
+    QXD_LAUNCHED("k_maxpy_norm");
+    int rc = finish(red, 1, st);
+    if (rc) return rc;
+    *nrm2 = red.h_res[0];
+    return QXD_OK;
+}
+
+template <typename T>
+int blas_caxpy(size_t n, cd c, const T* x, T* y, cudaStream_t st) {
+    k_caxpy<T><<<ew_blocks(n), 256, 0, st>>>(n, c.real(), c.imag(), x, y);
+    QXD_LAUNCHED("k_caxpy");
+    return QXD_OK;
+}
+
+template <typename T>
+int blas_scale(size_t n, double s, T* x, cudaStream_t st) {
+    k_scale<T><<<ew_blocks(n), 256, 0, st>>>(n, s, x);
+    QXD_LAUNCHED("k_scale");
+    return QXD_OK;
+}
+
+template <typename T>
+int blas_update_x(size_t n, int k, const CoefList& c, const VecList<T>& vs, double2* x, cudaStream_t st) {
+    if (k <= 0) return QXD_OK;
+    k_update_x<T><<<ew_blocks(n), 256, 0, st>>>(n, k, c, vs, x);
+    QXD_LAUNCHED("k_update_x");
+    return QXD_OK;
+}
+
+int blas_update_x_native32(size_t S, int k, const CoefList& c, const VecList<float2>& vs, double2* x,
+                           cudaStream_t st) {
+    if (k <= 0) return QXD_OK;
+    k_update_x_native32<<<ew_blocks(S), 256, 0, st>>>(S, k, c, vs, x);
+    QXD_LAUNCHED("k_update_x_native32");
+    return QXD_OK;
+}
+
+int blas_d2f_native(size_t S, const double2* in, float2* out, cudaStream_t st) {
+    k_d2f_native<<<ew_blocks(S), 256, 0, st>>>(S, in, out);
+    QXD_LAUNCHED("k_d2f_native");
+    return QXD_OK;
+}
+
+int blas_sub_norm(Reducer& red, size_t n, const double2* b, const double2* t, double2* r, double* nrm2,
+                  cudaStream_t st) {
+    k_sub_norm<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, b, t, r, red.partials);
+    QXD_LAUNCHED("k_sub_norm");
+    int rc = finish(red, 1, st);
+    if (rc) return rc;
+    *nrm2 = red.h_res[0];
+    return QXD_OK;
+}
+
+int blas_d2f(size_t n, const double2* in, float2* out, cudaStream_t st) {
+    k_d2f<<<ew_blocks(n), 256, 0, st>>>(n, in, out);
+    QXD_LAUNCHED("k_d2f");
+    return QXD_OK;
+}
+
+int blas_f2d(size_t n, const float2* in, double2* out, cudaStream_t st) {
+    k_f2d<<<ew_blocks(n), 256, 0, st>>>(n, in, out);
+    QXD_LAUNCHED("k_f2d");
+    return QXD_OK;
+}
+
+#define QXD_BLAS_INST(T)                                                                                  \
+    template int blas_mdot<T>(Reducer&, size_t, int, const VecList<T>&, const T*, cd*, cudaStream_t);   \
+    template int blas_norm2<T>(Reducer&, size_t, const T*, double*, cudaStream_t);                      \
+    template int blas_maxpy_norm<T>(Reducer&, size_t, int, const CoefList&, const VecList<T>&, T*,      \
+                                    double*, cudaStream_t);                                             \
+    template int blas_caxpy<T>(size_t, cd, const T*, T*, cudaStream_t);                                 \
+    template int blas_scale<T>(size_t, double, T*, cudaStream_t);                                       \
+    template int blas_update_x<T>(size_t, int, const CoefList&, const VecList<T>&, double2*, cudaStream_t);
+QXD_BLAS_INST(float2)
+QXD_BLAS_INST(double2)
+
+}  // namespace qxd

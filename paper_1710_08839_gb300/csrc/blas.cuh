@@ -1,0 +1,69 @@
+// Vector kernels of the Krylov solvers on flat complex arrays (FP32 as
+// float2, FP64 as double2). Inner products and norms accumulate in FP64 and
+// are reduced deterministically: a fixed grid writes per-block partial sums,
+// one block adds them in a fixed order, so the result does not depend on
+// timing or on other work on the GPU.
+#pragma once
+
+#include <complex>
+
+#include "qxd_internal.cuh"
+
+namespace qxd {
+
+constexpr int BLAS_KMAX = 16;       // vectors per multi-vector operation
+constexpr int RED_BLOCKS = 608;     // 4 x 152 SMs
+constexpr int RED_THREADS = 256;
+
+template <typename T>
+struct VecList {
+    const T* p[BLAS_KMAX];
+};
+struct CoefList {
+    double re[BLAS_KMAX];
+    double im[BLAS_KMAX];
+};
+
+// device workspace of the reductions
+struct Reducer {
+    double* partials = nullptr;  // [RED_BLOCKS][2 * BLAS_KMAX]
+    double* d_res = nullptr;     // [2 * BLAS_KMAX]
+    double* h_res = nullptr;     // pinned host copy
+    int init();
+    void release();
+};
+
+using cd = std::complex<double>;
+
+// out[j] = <x_j, y> = sum conj(x_j) y, j < k   (synchronises the stream)
+template <typename T>
+int blas_mdot(Reducer& red, size_t n, int k, const VecList<T>& xs, const T* y, cd* out, cudaStream_t st);
+// |x|^2
+template <typename T>
+int blas_norm2(Reducer& red, size_t n, const T* x, double* out, cudaStream_t st);
+// y -= sum_j c_j x_j ; returns |y|^2
+template <typename T>
+int blas_maxpy_norm(Reducer& red, size_t n, int k, const CoefList& c, const VecList<T>& xs, T* y, double* nrm2,
+                    cudaStream_t st);
+// y -= c x (no reduction)
+template <typename T>
+int blas_caxpy(size_t n, cd c, const T* x, T* y, cudaStream_t st);
+// x *= s
+template <typename T>
+int blas_scale(size_t n, double s, T* x, cudaStream_t st);
+// x64 += sum_j c_j v_j  (v_j in precision T)
+template <typename T>
+int blas_update_x(size_t n, int k, const CoefList& c, const VecList<T>& vs, double2* x, cudaStream_t st);
+// r = b - t, returns |r|^2
+int blas_sub_norm(Reducer& red, size_t n, const double2* b, const double2* t, double2* r, double* nrm2,
+                  cudaStream_t st);
+// native FP64 -> native FP32 spinor layout (S sites) and x64 += sum_j c_j v_j
+// with v_j native FP32 spinors; the two layouts order components differently
+int blas_d2f_native(size_t S, const double2* in, float2* out, cudaStream_t st);
+int blas_update_x_native32(size_t S, int k, const CoefList& c, const VecList<float2>& vs, double2* x,
+                           cudaStream_t st);
+// elementwise precision conversion (same element order)
+int blas_d2f(size_t n, const double2* in, float2* out, cudaStream_t st);
+int blas_f2d(size_t n, const float2* in, double2* out, cudaStream_t st);
+
+}  // namespace qxd

@@ -19,44 +19,8 @@ namespace qxd {
 
 namespace {
 
-template <typename R, bool QNZ, int MU>
-__device__ __forceinline__ void dirac_dir(const Geom& g, const Fields<R>& f, R q, int x0, int x1, int x2,
-                                          int x3, int s, int po, const R* afwd, cplx<R> acc[12]) {
-    cplx<R> v[12], h0[3], h1[3], g0[3], g1[3], u[3][3];
-    // forward hop: (1 - g_mu) U(x,mu) z(x,mu)^q psi(x+mu)
-    {
-        const int sn = native_index(g, neighbour_lex<MU, +1>(g, x0, x1, x2, x3), po);
-        load_spinor(f.psi, g.V, sn, v);
-        project<R, MU, +1>(v, h0, h1);
-        load_link(f.U, g.V, MU, s, u);
-        su3_mul(u, h0, g0);
-        su3_mul(u, h1, g1);
-        if (QNZ) {
-            cplx<R> ph = phase_of(q * afwd[MU]);
-            times3(ph, g0);
-            times3(ph, g1);
-        }
-        accumulate<R, MU, +1>(acc, g0, g1);
-    }
-    // backward hop: (1 + g_mu) U(x-mu,mu)^+ z(x-mu,mu)^-q psi(x-mu)
-    {
-        const int sb = native_index(g, neighbour_lex<MU, -1>(g, x0, x1, x2, x3), po);
-        load_spinor(f.psi, g.V, sb, v);
-        project<R, MU, -1>(v, h0, h1);
-        load_link(f.U, g.V, MU, sb, u);
-        su3_dag_mul(u, h0, g0);
-        su3_dag_mul(u, h1, g1);
-        if (QNZ) {
-            cplx<R> ph = conj(phase_of(q * load_angle(f.A, g.V, MU, sb)));
-            times3(ph, g0);
-            times3(ph, g1);
-        }
-        accumulate<R, MU, -1>(acc, g0, g1);
-    }
-}
-
 template <typename R, bool QNZ>
-__global__ void __launch_bounds__(DW_THREADS) k_dirac(Geom g, Fields<R> f, R q) {
+__global__ void __launch_bounds__(DW_THREADS, DwMinBlocks<R>::value) k_dirac(Geom g, Fields<R> f, R q) {
     const int tau = blockIdx.x * blockDim.x + threadIdx.x;
     if (tau >= g.V) return;
     int x0, x1, x2, x3;
@@ -64,15 +28,13 @@ __global__ void __launch_bounds__(DW_THREADS) k_dirac(Geom g, Fields<R> f, R q) 
     const int p = (x0 + x1 + x2 + x3) & 1;
     const int s = native_index(g, lex_index(g, x0, x1, x2, x3), p);
     const int po = 1 - p;
-    R afwd[4] = {0, 0, 0, 0};
-    if (QNZ) load_angles4(f.A, g.V, s, afwd);
     cplx<R> acc[12];
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = mk<R>(0, 0);
-    dirac_dir<R, QNZ, 0>(g, f, q, x0, x1, x2, x3, s, po, afwd, acc);
-    dirac_dir<R, QNZ, 1>(g, f, q, x0, x1, x2, x3, s, po, afwd, acc);
-    dirac_dir<R, QNZ, 2>(g, f, q, x0, x1, x2, x3, s, po, afwd, acc);
-    dirac_dir<R, QNZ, 3>(g, f, q, x0, x1, x2, x3, s, po, afwd, acc);
+    dirac_dir<R, QNZ, 0>(g, f, f.psi, g.V, 0, q, x0, x1, x2, x3, s, po, acc);
+    dirac_dir<R, QNZ, 1>(g, f, f.psi, g.V, 0, q, x0, x1, x2, x3, s, po, acc);
+    dirac_dir<R, QNZ, 2>(g, f, f.psi, g.V, 0, q, x0, x1, x2, x3, s, po, acc);
+    dirac_dir<R, QNZ, 3>(g, f, f.psi, g.V, 0, q, x0, x1, x2, x3, s, po, acc);
     cplx<R> v[12], w[12];
     load_spinor(f.psi, g.V, s, v);
     clover_mul(f.C, g.V, s, v, w);
@@ -122,7 +84,7 @@ int launch_dirac(qxd_lattice* lat, void* out, const void* in, int prec, cudaStre
         if (qnz) k_dirac<float, true><<<blocks, DW_THREADS, 0, st>>>(g, f, (float)lat->qhat);
         else k_dirac<float, false><<<blocks, DW_THREADS, 0, st>>>(g, f, 0.f);
     } else {
-        Fields<double> f{(const double2*)in, (double2*)out, lat->U64, lat->A64, lat->C64};
+        Fields<double> f{(const double2*)in, (double2*)out, lat->U64, lat->Z64, lat->C64};
         if (qnz) k_dirac<double, true><<<blocks, DW_THREADS, 0, st>>>(g, f, (double)lat->qhat);
         else k_dirac<double, false><<<blocks, DW_THREADS, 0, st>>>(g, f, 0.0);
     }

@@ -10,12 +10,21 @@ namespace qxd {
 
 constexpr int DW_THREADS = 256;
 
+// Register budget of the stencil kernels: FP32 at most 80 registers (3 blocks
+// of 256 threads per SM); the kernels are latency bound and more resident
+// warps keep more loads in flight. FP64 at most 128 (2 blocks).
+template <typename R>
+struct DwMinBlocks {
+    static constexpr int value = sizeof(R) == 4 ? 3 : 2;
+};
+
 template <typename R>
 struct Fields;
 
 template <>
 struct Fields<float> {
     using vec = float4;
+    using cvec = float4;
     const float4* __restrict__ psi;
     float4* __restrict__ out;
     const float4* __restrict__ U;  // [4][3][V] two rows
@@ -26,10 +35,11 @@ struct Fields<float> {
 template <>
 struct Fields<double> {
     using vec = double2;
+    using cvec = double;
     const double2* __restrict__ psi;
     double2* __restrict__ out;
     const double2* __restrict__ U;  // [4][9][V]
-    const double* __restrict__ A;   // [4][V]
+    const double2* __restrict__ A;  // [4][V] z = exp(i A) as (cos A, sin A)
     const double* __restrict__ C;   // [72][V]
 };
 
@@ -86,34 +96,32 @@ __device__ __forceinline__ void load_link(const double2* __restrict__ U, int V, 
     }
 }
 
-__device__ __forceinline__ float load_angle(const float4* __restrict__ A, int V, int mu, int s) {
-    const float* a = reinterpret_cast<const float*>(A + s);
-    return a[mu];
-}
-__device__ __forceinline__ double load_angle(const double* __restrict__ A, int V, int mu, int s) {
-    return A[(size_t)mu * V + s];
-}
-__device__ __forceinline__ void load_angles4(const float4* __restrict__ A, int V, int s, float a[4]) {
-    float4 t = A[s];
-    a[0] = t.x;
-    a[1] = t.y;
-    a[2] = t.z;
-    a[3] = t.w;
-}
-__device__ __forceinline__ void load_angles4(const double* __restrict__ A, int V, int s, double a[4]) {
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) a[mu] = A[(size_t)mu * V + s];
-}
-
-__device__ __forceinline__ cplx<float> phase_of(float t) {
+// U(1) factor z(x,mu)^qhat of the hopping term.
+// FP32: from the stored angle, exp(i qhat A). The argument is reduced to
+// [-pi, pi] (|A| <= pi, so only a few periods are removed) and evaluated with
+// the hardware approximation __sincosf, whose absolute error there is ~1e-6,
+// well inside the FP32 tolerance of the operator.
+// FP64: from the stored z = (cos A, sin A), z^qhat by binary powering
+// (|z| = 1, so z^-n = conj(z^n)).
+__device__ __forceinline__ cplx<float> link_phase(const float4* __restrict__ A, int V, int mu, int s, float q) {
+    float t = q * reinterpret_cast<const float*>(A + s)[mu];
+    const float k = rintf(t * 0.15915494309189535f);
+    t = fmaf(-k, 6.2831853071795865f, t);
     float sn, cs;
-    sincosf(t, &sn, &cs);
+    __sincosf(t, &sn, &cs);
     return mk(cs, sn);
 }
-__device__ __forceinline__ cplx<double> phase_of(double t) {
-    double sn, cs;
-    sincos(t, &sn, &cs);
-    return mk(cs, sn);
+__device__ __forceinline__ cplx<double> link_phase(const double2* __restrict__ Z, int V, int mu, int s, double q) {
+    const double2 zz = Z[(size_t)mu * V + s];
+    cplx<double> b = mk(zz.x, zz.y), r = mk(1.0, 0.0);
+    const int qi = (int)q;
+    int n = qi < 0 ? -qi : qi;
+    while (n) {
+        if (n & 1) r = r * b;
+        b = b * b;
+        n >>= 1;
+    }
+    return qi < 0 ? conj(r) : r;
 }
 
 template <typename R>
@@ -236,5 +244,48 @@ __device__ __forceinline__ void clover_mul(const double* __restrict__ C, int V, 
         herm6_mul(d, L, v + 6 * blk, w + 6 * blk);
     }
 }
+
+// The two hops of direction MU at site x (native index s, parity 1 - po),
+// raw sum (without the factor -1/2) added to acc. The neighbour spinors are
+// read from psi at index (native index - poff) with stride pstride, so the
+// same code serves full-lattice and half-lattice fields.
+template <typename R, bool QNZ, int MU>
+__device__ __forceinline__ void dirac_dir(const Geom& g, const Fields<R>& f,
+                                          const typename Fields<R>::vec* __restrict__ psi, int pstride,
+                                          int poff, R q, int x0, int x1, int x2, int x3, int s, int po,
+                                          cplx<R> acc[12]) {
+    cplx<R> v[12], h0[3], h1[3], g0[3], g1[3], u[3][3];
+    // forward hop: (1 - g_mu) U(x,mu) z(x,mu)^q psi(x+mu)
+    {
+        const int sn = native_index(g, neighbour_lex<MU, +1>(g, x0, x1, x2, x3), po);
+        load_spinor(psi, pstride, sn - poff, v);
+        project<R, MU, +1>(v, h0, h1);
+        load_link(f.U, g.V, MU, s, u);
+        su3_mul(u, h0, g0);
+        su3_mul(u, h1, g1);
+        if (QNZ) {
+            cplx<R> ph = link_phase(f.A, g.V, MU, s, q);
+            times3(ph, g0);
+            times3(ph, g1);
+        }
+        accumulate<R, MU, +1>(acc, g0, g1);
+    }
+    // backward hop: (1 + g_mu) U(x-mu,mu)^+ z(x-mu,mu)^-q psi(x-mu)
+    {
+        const int sb = native_index(g, neighbour_lex<MU, -1>(g, x0, x1, x2, x3), po);
+        load_spinor(psi, pstride, sb - poff, v);
+        project<R, MU, -1>(v, h0, h1);
+        load_link(f.U, g.V, MU, sb, u);
+        su3_dag_mul(u, h0, g0);
+        su3_dag_mul(u, h1, g1);
+        if (QNZ) {
+            cplx<R> ph = conj(link_phase(f.A, g.V, MU, sb, q));
+            times3(ph, g0);
+            times3(ph, g1);
+        }
+        accumulate<R, MU, -1>(acc, g0, g1);
+    }
+}
+
 
 }  // namespace qxd

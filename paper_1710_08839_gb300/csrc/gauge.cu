@@ -68,7 +68,8 @@ __device__ __forceinline__ M3 dag(const M3& x) {
 __global__ void k_gauge_ingest(Geom g, int L1phys, int cstar1, const double* __restrict__ su3,
                                const double* __restrict__ ang, int extended, double2* __restrict__ U64,
                                float4* __restrict__ U32, double* __restrict__ A64,
-                               float4* __restrict__ A32, int* __restrict__ bad) {
+                               double2* __restrict__ Z64, float4* __restrict__ A32,
+                               int* __restrict__ bad) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.V) return;
     int x0, x1, x2, x3;
@@ -124,6 +125,9 @@ __global__ void k_gauge_ingest(Geom g, int L1phys, int cstar1, const double* __r
         U32[((size_t)mu * 3 + 2) * V + s] =
             make_float4((float)u[1][1].re, (float)u[1][1].im, (float)u[1][2].re, (float)u[1][2].im);
         A64[(size_t)mu * V + s] = a;
+        double sa, ca;
+        sincos(a, &sa, &ca);
+        Z64[(size_t)mu * V + s] = make_double2(ca, sa);
         a32[mu] = (float)a;
     }
     A32[s] = make_float4(a32[0], a32[1], a32[2], a32[3]);
@@ -272,7 +276,7 @@ int launch_gauge_ingest(qxd_lattice* lat, const double* su3, const double* ang, 
     const int cstar1 = (lat->cstar_mask & 2u) ? 1 : 0;
     int blocks = (g.V + 127) / 128;
     k_gauge_ingest<<<blocks, 128, 0, lat->stream>>>(g, lat->L1, cstar1, su3, ang, extended, lat->U64,
-                                                    lat->U32, lat->A64, lat->A32, d_bad);
+                                                    lat->U32, lat->A64, lat->Z64, lat->A32, d_bad);
     QXD_LAUNCHED("k_gauge_ingest");
     if (kind == QXD_GAUGE_EXTENDED_CHECKED && cstar1) {
         k_check_admissible<<<blocks, 128, 0, lat->stream>>>(g, su3, ang, d_bad);

@@ -8,7 +8,7 @@
 
 #include <string>
 
-#include "../../include/qxd.h"
+#include "qxd.h"
 
 namespace qxd {
 
@@ -79,6 +79,23 @@ __host__ __device__ __forceinline__ void sweep_coords(const Geom& g, int tau, in
     x2 = chunk * g.R + r;
 }
 
+// sweep over the sites of one parity p (tau < Vh), same tiled order
+__host__ __device__ __forceinline__ void sweep_coords_parity(const Geom& g, int p, int tau, int& x0, int& x1,
+                                                             int& x2, int& x3) {
+    const int half = g.N3 >> 1;
+    const int rowlen = g.R * half;
+    int within = tau % rowlen;
+    int rest = tau / rowlen;
+    x1 = rest % g.N1;
+    rest /= g.N1;
+    x0 = rest % g.N0;
+    int chunk = rest / g.N0;
+    int r = within / half;
+    int j = within - r * half;
+    x2 = chunk * g.R + r;
+    x3 = 2 * j + ((x0 + x1 + x2 + p) & 1);
+}
+
 // coordinates of the site with native index s
 __host__ __device__ __forceinline__ void native_coords(const Geom& g, int s, int& x0, int& x1, int& x2, int& x3) {
     int p = s >= g.Vh;
@@ -134,6 +151,7 @@ __host__ __device__ __forceinline__ int neighbour_lex(const Geom& g, int x0, int
 // links  FP64 : double2 U[4][9][V]  full 3x3, row major
 // angle  FP32 : float4  A[V]        A(x, mu), mu = 0..3
 // angle  FP64 : double  A[4][V]
+// phase  FP64 : double2 Z[4][V]    z = exp(i A) as (cos A, sin A)
 // clover FP32 : float4  C[18][V]    two Hermitian 6x6 blocks (spins {0,1},
 //                                   then {2,3}), 36 floats each: 6 real
 //                                   diagonals, then the 15 complex entries
@@ -194,6 +212,7 @@ __host__ __device__ __forceinline__ cplx<R> times_mi(cplx<R> a) { return {a.im, 
 // ---------------------------------------------------------------------------
 // the lattice object
 // ---------------------------------------------------------------------------
+struct SolverWork;
 }  // namespace qxd
 
 struct qxd_lattice {
@@ -207,6 +226,7 @@ struct qxd_lattice {
     double2* U64 = nullptr;  // [4][9][V]
     float4* U32 = nullptr;   // [4][3][V]
     double* A64 = nullptr;   // [4][V]
+    double2* Z64 = nullptr;  // [4][V] exp(i A)
     float4* A32 = nullptr;   // [V]
     double* ftens = nullptr; // [60][V]
     bool has_gauge = false;
@@ -226,6 +246,8 @@ struct qxd_lattice {
     void* scratch_in = nullptr;   // native spinor FP64-sized
     void* scratch_out = nullptr;  // native spinor FP64-sized
     void* scratch_lex = nullptr;  // lexicographic FP64 spinor
+
+    qxd::SolverWork* solver = nullptr;  // Krylov work vectors (first solve)
 };
 
 namespace qxd {
@@ -237,4 +259,6 @@ int launch_clover_build(qxd_lattice* lat, int* d_bad);
 int launch_dirac(qxd_lattice* lat, void* out, const void* in, int prec, cudaStream_t st);
 int launch_pack(qxd_lattice* lat, void* nat, const void* lex, int prec, cudaStream_t st);
 int launch_unpack(qxd_lattice* lat, void* lex, const void* nat, int prec, cudaStream_t st);
+int ensure_scratch(qxd_lattice* lat);
+void release_solver(qxd_lattice* lat);
 }  // namespace qxd

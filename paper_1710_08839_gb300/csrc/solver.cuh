@@ -1,0 +1,45 @@
+// Solver workspace and the Schwarz (SAP) preconditioner interface.
+#pragma once
+
+#include "blas.cuh"
+#include "qxd_internal.cuh"
+
+namespace qxd {
+
+// block decomposition of the SAP preconditioner: 4^4 blocks, coloured by the
+// parity of the block coordinates
+struct SapGeom {
+    int nb0, nb1, nb2, nb3;
+    int nblk;   // all blocks
+    int nhalf;  // blocks of one colour
+};
+
+struct SapWork {
+    SapGeom sg{};
+};
+
+struct SolverWork {
+    int V = 0, nkv = 0, prec = -1;
+    void *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *t64 = nullptr;  // full-lattice FP64
+    void *xs = nullptr, *rs = nullptr, *ts = nullptr, *bs = nullptr;      // system vectors FP64
+    void* tmp64 = nullptr;                                                // odd-parity FP64 temp
+    void* tmp_in = nullptr;                                               // inner-precision temp
+    void* rin = nullptr;                                                  // inner residual
+    void* phi[BLAS_KMAX] = {};
+    void* chi[BLAS_KMAX] = {};
+    Reducer red;
+    SapWork sap;
+    int ensure(int V, int nkv, int prec);
+    void release();
+};
+
+// checks that the lattice admits the 4^4 SAP block colouring
+int sap_check(qxd_lattice* lat);
+// out = SAP(in): ncy cycles of the multiplicative Schwarz method over the
+// black and white blocks, nmr minimal-residual steps per block solve
+template <typename R>
+int sap_apply(qxd_lattice* lat, SapWork& w, void* out, const void* in, int ncy, int nmr, cudaStream_t st);
+
+int run_solve(qxd_lattice* lat, const qxd_solver_params& P, qxd_solve_info& info, cudaStream_t st);
+
+}  // namespace qxd

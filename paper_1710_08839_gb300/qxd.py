@@ -35,6 +35,11 @@ QXD_GAUGE_EXTENDED_CHECKED = 0x1
 QXD_GAUGE_EXTENDED_UNCHECKED = 0x2
 QXD_GAUGE_HOST = 0x10
 
+QXD_PRECOND_NONE = 0
+QXD_PRECOND_SAP = 1
+QXD_SOLVE_FULL = 0
+QXD_SOLVE_EO = 1
+
 _STATUS_NAMES = {
     0: "QXD_OK", -1: "QXD_ERR_ARG", -2: "QXD_ERR_OOM", -3: "QXD_ERR_CUDA",
     -4: "QXD_ERR_NOT_ADMISSIBLE", -5: "QXD_ERR_SW_SINGULAR", -6: "QXD_ERR_NOT_CONVERGED",
@@ -53,6 +58,19 @@ _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _d = ctypes.c_double
 
+
+class qxd_solver_params(ctypes.Structure):
+    _fields_ = [("tol", _d), ("max_iter", _i), ("nkv", _i), ("precond", _i), ("system", _i),
+                ("inner_prec", _i), ("sap_ncy", _i), ("sap_nmr", _i), ("delta", _d), ("flags", _i)]
+
+
+class qxd_solve_info(ctypes.Structure):
+    _fields_ = [("status", _i), ("iterations", _i), ("restarts", _i), ("true_relres", _d),
+                ("time_ms", _d), ("dw64_calls", _i), ("inner_calls", _i)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
 # name -> (restype, argtypes); mirrors include/qxd.h
 SIGNATURES = {
     "qxd_lattice_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, ctypes.c_uint, _vp]),
@@ -62,6 +80,12 @@ SIGNATURES = {
     "qxd_set_params": (_i, [_vp, _d, _d, _d, _i]),
     "qxd_sw_build": (_i, [_vp]),
     "qxd_Dw": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "qxd_Dhat": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "qxd_eo_prepare": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "qxd_eo_reconstruct": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "qxd_sap": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
+    "qxd_solver_defaults": (None, [ctypes.POINTER(qxd_solver_params)]),
+    "qxd_solve": (_i, [_vp, _vp, _vp, ctypes.POINTER(qxd_solver_params), ctypes.POINTER(qxd_solve_info), _vp]),
     "qxd_spinor_bytes": (ctypes.c_size_t, [_vp, _i]),
     "qxd_spinor_pack": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_spinor_unpack": (_i, [_vp, _vp, _vp, _i, _vp]),
@@ -133,6 +157,37 @@ def qxd_spinor_pack(lat, nat_ptr, lex_ptr, prec, stream=0) -> int:
 
 def qxd_spinor_unpack(lat, lex_ptr, nat_ptr, prec, stream=0) -> int:
     return check(_call("qxd_spinor_unpack", lat, lex_ptr, nat_ptr, prec, stream))
+
+
+def qxd_Dhat(lat, out_ptr, in_ptr, flags, stream=0) -> int:
+    return check(_call("qxd_Dhat", lat, out_ptr, in_ptr, flags, stream))
+
+
+def qxd_eo_prepare(lat, out_ptr, b_ptr, flags, stream=0) -> int:
+    return check(_call("qxd_eo_prepare", lat, out_ptr, b_ptr, flags, stream))
+
+
+def qxd_eo_reconstruct(lat, x_ptr, b_ptr, flags, stream=0) -> int:
+    return check(_call("qxd_eo_reconstruct", lat, x_ptr, b_ptr, flags, stream))
+
+
+def qxd_sap(lat, out_ptr, in_ptr, ncy, nmr, flags, stream=0) -> int:
+    return check(_call("qxd_sap", lat, out_ptr, in_ptr, ncy, nmr, flags, stream))
+
+
+def qxd_solver_defaults() -> qxd_solver_params:
+    p = qxd_solver_params()
+    _call("qxd_solver_defaults", ctypes.byref(p))
+    return p
+
+
+def qxd_solve(lat, x_ptr, b_ptr, params: qxd_solver_params, stream=0):
+    """Returns (status, info); status QXD_ERR_NOT_CONVERGED does not raise."""
+    info = qxd_solve_info()
+    rc = _call("qxd_solve", lat, x_ptr, b_ptr, ctypes.byref(params), ctypes.byref(info), stream)
+    if rc not in (QXD_OK, QXD_ERR_NOT_CONVERGED):
+        check(rc)
+    return rc, info
 
 
 def qxd_last_error() -> str:
@@ -230,6 +285,44 @@ class Lattice:
             raise ValueError("spinors must be contiguous")
         qxd_Dw(self.handle, out.data_ptr(), inp.data_ptr(), flags, _stream_ptr(stream))
         return out
+
+    @staticmethod
+    def _prec_of(t):
+        torch = _torch()
+        return QXD_FP32 if t.dtype in (torch.complex64, torch.float32) else QXD_FP64
+
+    def Dhat(self, out, inp, native=False, stream=None):
+        flags = self._prec_of(inp) | (QXD_LAYOUT_NATIVE if native else 0)
+        qxd_Dhat(self.handle, out.data_ptr(), inp.data_ptr(), flags, _stream_ptr(stream))
+        return out
+
+    def eo_prepare(self, out, b, native=False, stream=None):
+        flags = self._prec_of(b) | (QXD_LAYOUT_NATIVE if native else 0)
+        qxd_eo_prepare(self.handle, out.data_ptr(), b.data_ptr(), flags, _stream_ptr(stream))
+        return out
+
+    def eo_reconstruct(self, x, b, native=False, stream=None):
+        flags = self._prec_of(b) | (QXD_LAYOUT_NATIVE if native else 0)
+        qxd_eo_reconstruct(self.handle, x.data_ptr(), b.data_ptr(), flags, _stream_ptr(stream))
+        return x
+
+    def sap(self, out, inp, ncy=5, nmr=5, native=False, prec=None, stream=None):
+        flags = (self._prec_of(inp) if prec is None else prec) | (QXD_LAYOUT_NATIVE if native else 0)
+        qxd_sap(self.handle, out.data_ptr(), inp.data_ptr(), ncy, nmr, flags, _stream_ptr(stream))
+        return out
+
+    def solve(self, x, b, stream=None, **kw):
+        """Solve D x = b (FP64 complex128 tensors). Keyword arguments override
+        the fields of qxd_solver_params. Returns (status, info dict)."""
+        p = qxd_solver_defaults()
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown solver parameter {k}")
+            setattr(p, k, v)
+        if b.device.type == "cpu":
+            p.flags |= QXD_HOST
+        rc, info = qxd_solve(self.handle, x.data_ptr(), b.data_ptr(), p, _stream_ptr(stream))
+        return rc, info.as_dict()
 
     def pack(self, native_out, lex_in, prec, stream=None):
         qxd_spinor_pack(self.handle, native_out.data_ptr(), lex_in.data_ptr(), prec, _stream_ptr(stream))
