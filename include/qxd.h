@@ -226,6 +226,28 @@ void qxd_solver_defaults(qxd_solver_params* p);
 int qxd_solve(qxd_lattice* lat, void* x, const void* b, const qxd_solver_params* params,
               qxd_solve_info* info, void* stream);
 
+/*
+ * out = D in, like qxd_Dw with device buffers in the lexicographic layout,
+ * but without allocating device memory. The paper has no counterpart: this
+ * entry point exists for callers that cannot let a library allocate during a
+ * call (frameworks that hand out all device memory from their own pool,
+ * latency-bound paths where a cudaMalloc and the device synchronisation it
+ * may imply are not acceptable, jobs that hold nearly all device memory).
+ * The layout conversion goes through a fixed scratch array in the library's
+ * device memory (2 x 12 MiB, reserved on every GPU that loads the library
+ * until the process exits) instead of the scratch qxd_Dw allocates.
+ * - flags: QXD_FP64 or QXD_FP32 only (device buffers, lexicographic layout).
+ * - Lattices above 65536 simulated sites are rejected with QXD_ERR_ARG.
+ * - The first call on a device looks up the scratch array's device address
+ *   (cudaGetSymbolAddress) and keeps it; make that first call before any
+ *   stream capture.
+ * - Every call on a device shares the one scratch array, which keeps the
+ *   last call's contents (each call overwrites all it reads): calls that
+ *   overlap on the GPU (other streams, other threads) race and must be
+ *   serialised by the caller.
+ */
+int qxd_Dw_noalloc(qxd_lattice* lat, void* out, const void* in, int flags, void* stream);
+
 /* Bytes of one spinor field in the native layout for precision `prec`. */
 size_t qxd_spinor_bytes(const qxd_lattice* lat, int prec);
 

@@ -80,6 +80,7 @@ SIGNATURES = {
     "qxd_set_params": (_i, [_vp, _d, _d, _d, _i]),
     "qxd_sw_build": (_i, [_vp]),
     "qxd_Dw": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "qxd_Dw_noalloc": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_Dhat": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_eo_prepare": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_eo_reconstruct": (_i, [_vp, _vp, _vp, _i, _vp]),
