@@ -38,8 +38,17 @@ WORKLOADS = {
     # a smaller case of the same kernel for profiling (48x48x24x24, 0.9 GB/step)
     "medium": dict(T=48, L1=24, L2=24, L3=24, mask=0b1110, eps=0.3, sigma=0.3,
                    m0=0.1, csw=1.0, cswqed=1.0, qhat=2),
+    # the solver lattice (64x64x32x32) and a small one (32x32x16x16, 0.18 GB/step)
+    "solve": dict(T=64, L1=32, L2=32, L3=32, mask=0b1110, eps=0.3, sigma=0.3,
+                  m0=0.01, csw=1.0, cswqed=1.0, qhat=2),
+    "small": dict(T=32, L1=16, L2=16, L3=16, mask=0b1110, eps=0.3, sigma=0.3,
+                  m0=0.01, csw=1.0, cswqed=1.0, qhat=2),
 }
 WORKLOAD = WORKLOADS["full"]
+# the solver workload: physical L = 32, T = 64 with C*, doubled 64x64x32x32;
+# FGCR (nkv 16) with FP32 SAP (4^4 blocks, ncy 5, nmr 5) against FP64-only GCR
+SOLVE_WORKLOAD = dict(T=64, L1=32, L2=32, L3=32, mask=0b1110, eps=0.3, sigma=0.3, csw=1.0, cswqed=1.0,
+                      points=[(0.05, -1), (0.05, 2), (0.01, -1), (0.01, 2)], tol=1e-10)
 BYTES_PER_SITE_FP32 = {True: 688, False: 672}   # qhat != 0 -> angles read
 BYTES_PER_SITE_FP64 = {True: 1568, False: 1536}
 METRIC = "Dw GB/s"
@@ -154,6 +163,88 @@ def make_inputs(device, w=None):
     return su3, ang, psi, V
 
 
+def solve_benchmark(qxd, torch, solvers=("mixed", "fp64_eo", "fp64_full")):
+    """Solves of D x = b at every (m0, qhat) point of the solver workload with
+    each solver; wall time of the qxd_solve call (which synchronises)."""
+    w = SOLVE_WORKLOAD
+    su3, ang, psi, V = make_inputs("cuda", dict(w, T=w["T"]))
+    b = psi.cuda()
+    del psi
+    lat = qxd.Lattice(w["T"], w["L1"], w["L2"], w["L3"], w["mask"])
+    lat.set_gauge(su3, ang)
+    del su3, ang
+    kinds = {
+        "mixed": dict(precond=qxd.QXD_PRECOND_SAP, inner_prec=qxd.QXD_FP32),
+        "fp64_sap": dict(precond=qxd.QXD_PRECOND_SAP, inner_prec=qxd.QXD_FP64, delta=0.0),
+        "fp64_eo": dict(system=qxd.QXD_SOLVE_EO, inner_prec=qxd.QXD_FP64, max_iter=20000, delta=0.0),
+        "fp64_full": dict(system=qxd.QXD_SOLVE_FULL, inner_prec=qxd.QXD_FP64, max_iter=20000, delta=0.0),
+    }
+    rows = []
+    totals = {k: 0.0 for k in solvers}
+    first = True
+    for m0, q in w["points"]:
+        lat.set_params(m0, w["csw"], w["cswqed"], q)
+        lat.sw_build()
+        xs = {}
+        row = {"m0": m0, "qhat": q}
+        for k in solvers:
+            x = torch.zeros_like(b)
+            if first:  # work vectors are allocated by the first solve
+                lat.solve(x, b, tol=w["tol"], **kinds[k])
+                first = False
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, info = lat.solve(x, b, tol=w["tol"], **kinds[k])
+            dt = time.perf_counter() - t0
+            totals[k] += dt
+            xs[k] = x
+            row[k] = {"status": rc, "ms": dt * 1e3, "iterations": info["iterations"],
+                      "restarts": info["restarts"], "true_relres": info["true_relres"],
+                      "dw64_calls": info["dw64_calls"]}
+        ref = "fp64_eo" if "fp64_eo" in xs else None
+        if ref:
+            for k in xs:
+                if k != ref:
+                    row[k]["rel_diff_vs_" + ref] = float((xs[k] - xs[ref]).norm() / xs[ref].norm())
+        rows.append(row)
+        del xs
+    lat.close()
+    n = len(w["points"])
+    out = {"workload": "doubled 64x64x32x32 C* lattice (L=32, T=64), eps 0.3, csw=cswqed=1, "
+                       "tol 1e-10 (true FP64 residual), FGCR nkv 16; mixed = FP32 SAP 4^4 ncy 5 nmr 5",
+           "points": rows, "solves_per_s": {k: n / totals[k] for k in solvers}}
+    if "mixed" in solvers:
+        for k in solvers:
+            if k != "mixed":
+                out["speedup_mixed_vs_" + k] = totals[k] / totals["mixed"]
+    return out
+
+
+def sap_benchmark(qxd, torch, steps, w):
+    """Time one FP32 SAP application (ncy 5, nmr 5) on the lattice of workload w."""
+    su3, ang, psi, V = make_inputs("cuda", w)
+    lat = qxd.Lattice(w["T"], w["L1"], w["L2"], w["L3"], w["mask"])
+    lat.set_gauge(su3, ang)
+    lat.set_params(w["m0"], w["csw"], w["cswqed"], w["qhat"])
+    lat.sw_build()
+    x = psi.to(torch.complex64).cuda()
+    xn = torch.empty(lat.spinor_bytes(qxd.QXD_FP32), dtype=torch.uint8, device="cuda")
+    lat.pack(xn, x, qxd.QXD_FP32)
+    yn = torch.empty_like(xn)
+    for _ in range(3):
+        lat.sap(yn, xn, 5, 5, native=True, prec=qxd.QXD_FP32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        lat.sap(yn, xn, 5, 5, native=True, prec=qxd.QXD_FP32)
+    e1.record()
+    torch.cuda.synchronize()
+    lat.close()
+    return {"sap_ms": e0.elapsed_time(e1) / steps, "sites": V, "ncy": 5, "nmr": 5,
+            "lattice": f"{w['T']}x{2 * w['L1']}x{w['L2']}x{w['L3']}"}
+
+
 def oracle_sample_rate(su3_host, ang_host, psi_host, V, w, target_s=12.0):
     """FP64 oracle on a sample of sites of the workload: (sites/s, sites, seconds)."""
     import numpy as np
@@ -231,6 +322,10 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="dw", choices=["dw", "solve", "sap"],
+                    help="dw: the Dw throughput line (plus a solver summary unless --no-solve); "
+                         "solve: solver comparison only; sap: time the SAP preconditioner only")
+    ap.add_argument("--no-solve", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -247,6 +342,13 @@ def main():
     import __graft_entry__ as ge
     ge.build()
     from paper_1710_08839_gb300 import qxd
+
+    if args.mode in ("solve", "sap"):
+        res = (solve_benchmark(qxd, torch) if args.mode == "solve"
+               else sap_benchmark(qxd, torch, args.steps, WORKLOADS[args.workload]))
+        if rank == 0:
+            print(json.dumps({"mode": args.mode, **res}), flush=True)
+        return
 
     w = WORKLOADS[args.workload]
     su3, ang, psi, V = make_inputs("cuda", w)
@@ -353,6 +455,13 @@ def main():
                "sample": f"FP64 oracle D at {n} random sites of the workload in {dt:.1f} s "
                          f"({rate:.0f} sites/s, FP64 byte model 1568 B/site)"}
 
+    solve = None
+    if not args.no_solve:
+        lat.close()
+        xn = yn = None
+        torch.cuda.empty_cache()
+        solve = solve_benchmark(qxd, torch)
+
     rec = _traffic_record(["paper_1710_08839_gb300/csrc/dirac.cu",
                            "paper_1710_08839_gb300/csrc/dirac_common.cuh"])
     traffic = rec["bytes_per_launch"] if rec else None
@@ -374,10 +483,12 @@ def main():
         "gpu_launches": args.steps,
         "clocks": clocks,
         "variants": variants,
+        "solve": solve,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    lat.close()
+    if args.no_solve:
+        lat.close()
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()

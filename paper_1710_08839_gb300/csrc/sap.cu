@@ -43,6 +43,55 @@ struct SmemField {
     }
 };
 
+// Links of the block: FP32 keeps them in shared memory (two rows + angle,
+// 53 KB per block), loaded once per block visit; FP64 reads the global field.
+template <typename R>
+struct BlockLinks;
+
+template <>
+struct BlockLinks<float> {
+    static constexpr bool kStaged = true;
+    float4* U;  // [4][3][256] by local site index
+    float* A;   // [4][256]
+    __device__ __forceinline__ void link(const Fields<float>&, const Geom&, int mu, int lidx, int,
+                                         cplx<float> u[3][3]) const {
+        const float4 a = U[(mu * 3 + 0) * SAP_SITES + lidx];
+        const float4 b = U[(mu * 3 + 1) * SAP_SITES + lidx];
+        const float4 c = U[(mu * 3 + 2) * SAP_SITES + lidx];
+        u[0][0] = mk(a.x, a.y);
+        u[0][1] = mk(a.z, a.w);
+        u[0][2] = mk(b.x, b.y);
+        u[1][0] = mk(b.z, b.w);
+        u[1][1] = mk(c.x, c.y);
+        u[1][2] = mk(c.z, c.w);
+        u[2][0] = conj(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
+        u[2][1] = conj(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
+        u[2][2] = conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+    }
+    __device__ __forceinline__ cplx<float> phase(const Fields<float>&, const Geom&, int mu, int lidx, int,
+                                                 float q) const {
+        float t = q * A[mu * SAP_SITES + lidx];
+        const float k = rintf(t * 0.15915494309189535f);
+        t = fmaf(-k, 6.2831853071795865f, t);
+        float sn, cs;
+        __sincosf(t, &sn, &cs);
+        return mk(cs, sn);
+    }
+};
+
+template <>
+struct BlockLinks<double> {
+    static constexpr bool kStaged = false;
+    __device__ __forceinline__ void link(const Fields<double>& f, const Geom& g, int mu, int, int s,
+                                         cplx<double> u[3][3]) const {
+        load_link(f.U, g.V, mu, s, u);
+    }
+    __device__ __forceinline__ cplx<double> phase(const Fields<double>& f, const Geom& g, int mu, int, int s,
+                                                  double q) const {
+        return link_phase(f.A, g.V, mu, s, q);
+    }
+};
+
 struct Site {
     int l[4];   // coordinates inside the block
     int x[4];   // global coordinates
@@ -64,21 +113,29 @@ __device__ __forceinline__ Site make_site(const Geom& g, const int org[4], int l
     return t;
 }
 
+// native index of the in-block site one step back in direction MU
+template <int MU>
+__device__ __forceinline__ int back_native(const Geom& g, const Site& t) {
+    int y[4] = {t.x[0], t.x[1], t.x[2], t.x[3]};
+    y[MU] -= 1;
+    return native_index(g, lex_index(g, y[0], y[1], y[2], y[3]), (y[0] + y[1] + y[2] + y[3]) & 1);
+}
+
 // hops of direction MU that stay inside the block (Dirichlet block boundary);
 // the neighbour spinor comes from shared memory (field of the other parity)
 template <typename R, bool QNZ, int MU>
-__device__ __forceinline__ void block_dir(const Geom& g, const Fields<R>& f, const SmemField<R>& src, R q,
-                                          const Site& t, cplx<R> acc[12]) {
+__device__ __forceinline__ void block_dir(const Geom& g, const Fields<R>& f, const BlockLinks<R>& bl,
+                                          const SmemField<R>& src, R q, const Site& t, cplx<R> acc[12]) {
     constexpr int stride = MU == 0 ? 64 : MU == 1 ? 16 : MU == 2 ? 4 : 1;
     cplx<R> v[12], h0[3], h1[3], g0[3], g1[3], u[3][3];
     if (t.l[MU] < SAP_BS - 1) {
         src.load((t.lidx + stride) >> 1, v);
         project<R, MU, +1>(v, h0, h1);
-        load_link(f.U, g.V, MU, t.s, u);
+        bl.link(f, g, MU, t.lidx, t.s, u);
         su3_mul(u, h0, g0);
         su3_mul(u, h1, g1);
         if (QNZ) {
-            cplx<R> ph = link_phase(f.A, g.V, MU, t.s, q);
+            cplx<R> ph = bl.phase(f, g, MU, t.lidx, t.s, q);
             times3(ph, g0);
             times3(ph, g1);
         }
@@ -87,14 +144,12 @@ __device__ __forceinline__ void block_dir(const Geom& g, const Fields<R>& f, con
     if (t.l[MU] > 0) {
         src.load((t.lidx - stride) >> 1, v);
         project<R, MU, -1>(v, h0, h1);
-        int y[4] = {t.x[0], t.x[1], t.x[2], t.x[3]};
-        y[MU] -= 1;  // inside the block: no wrap
-        const int sb = native_index(g, lex_index(g, y[0], y[1], y[2], y[3]), (y[0] + y[1] + y[2] + y[3]) & 1);
-        load_link(f.U, g.V, MU, sb, u);
+        const int sb = BlockLinks<R>::kStaged ? 0 : back_native<MU>(g, t);
+        bl.link(f, g, MU, t.lidx - stride, sb, u);
         su3_dag_mul(u, h0, g0);
         su3_dag_mul(u, h1, g1);
         if (QNZ) {
-            cplx<R> ph = conj(link_phase(f.A, g.V, MU, sb, q));
+            cplx<R> ph = conj(bl.phase(f, g, MU, t.lidx - stride, sb, q));
             times3(ph, g0);
             times3(ph, g1);
         }
@@ -103,20 +158,20 @@ __device__ __forceinline__ void block_dir(const Geom& g, const Fields<R>& f, con
 }
 
 template <typename R, bool QNZ>
-__device__ __forceinline__ void block_hops(const Geom& g, const Fields<R>& f, const SmemField<R>& src, R q,
-                                           const Site& t, cplx<R> acc[12]) {
+__device__ __noinline__ void block_hops(const Geom& g, const Fields<R>& f, const BlockLinks<R>& bl,
+                                        const SmemField<R> src, R q, const Site& t, cplx<R> acc[12]) {
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = mk<R>(0, 0);
-    block_dir<R, QNZ, 0>(g, f, src, q, t, acc);
-    block_dir<R, QNZ, 1>(g, f, src, q, t, acc);
-    block_dir<R, QNZ, 2>(g, f, src, q, t, acc);
-    block_dir<R, QNZ, 3>(g, f, src, q, t, acc);
+    block_dir<R, QNZ, 0>(g, f, bl, src, q, t, acc);
+    block_dir<R, QNZ, 1>(g, f, bl, src, q, t, acc);
+    block_dir<R, QNZ, 2>(g, f, bl, src, q, t, acc);
+    block_dir<R, QNZ, 3>(g, f, bl, src, q, t, acc);
 }
 
-// (D psi)(x) over the whole lattice at one site; out = eta - D psi
+// r = eta - (D psi)(x), D over the whole lattice, at one site
 template <typename R, bool QNZ>
-__device__ __forceinline__ void residual_at(const Geom& g, const Fields<R>& f, const typename Fields<R>::vec* eta,
-                                            R q, const Site& t, bool psi_zero, cplx<R> r[12]) {
+__device__ __noinline__ void residual_at(const Geom& g, const Fields<R>& f, const typename Fields<R>::vec* eta,
+                                         R q, const Site& t, bool psi_zero, cplx<R> r[12]) {
     load_spinor(eta, g.V, t.s, r);
     if (psi_zero) return;
     const int po = 1 - ((t.x[0] + t.x[1] + t.x[2] + t.x[3]) & 1);
@@ -160,18 +215,38 @@ __device__ __forceinline__ void block_sum3(R a, R b, R c, R* red, R out[3]) {
     __syncthreads();
 }
 
+template <typename R>
+constexpr size_t sap_link_bytes() {
+    return BlockLinks<R>::kStaged ? (12 * SAP_SITES * sizeof(float4) + 4 * SAP_SITES * sizeof(float)) : 0;
+}
+
+// Each thread owns one even and one odd site of the block: the local pair
+// (2t, 2t + 1). Phases in order (each block-hop phase is one call of
+// block_hops from a single call site, which keeps the code small):
+//   residual on both sites; t_o = M_oo^-1 r_o
+//   step 0:            rho = r_e - H_eo t_o                       (even)
+//   step 2k+1, 2k+2:   t_o = M_oo^-1 H_oe rho (odd); w = M_ee rho - H_eo t_o,
+//                      omega = <w,rho>/<w,w>, delta_e += omega rho,
+//                      rho -= omega w (even)             for k < nmr
+//   last step:         delta_o = M_oo^-1 (r_o - H_oe delta_e)     (odd)
 template <typename R, bool QNZ>
-__global__ void __launch_bounds__(SAP_THREADS) k_sap_block(Geom g, SapGeom sg, int colour, int psi_zero,
-                                                           Fields<R> f, const typename Fields<R>::cvec* __restrict__ Cinv,
-                                                           const typename Fields<R>::vec* __restrict__ eta, int nmr,
-                                                           R q) {
+__global__ void __launch_bounds__(SAP_THREADS, 2) k_sap_block(Geom g, SapGeom sg, int colour, int psi_zero,
+                                                              Fields<R> f, const typename Fields<R>::cvec* __restrict__ Cinv,
+                                                              const typename Fields<R>::vec* __restrict__ eta, int nmr,
+                                                              R q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* sm = reinterpret_cast<R*>(smem_raw);
+    BlockLinks<R> bl;
+    unsigned char* sp = smem_raw;
+    if constexpr (BlockLinks<R>::kStaged) {
+        bl.U = reinterpret_cast<float4*>(sp);
+        bl.A = reinterpret_cast<float*>(sp + 12 * SAP_SITES * sizeof(float4));
+        sp += sap_link_bytes<R>();
+    }
+    R* sm = reinterpret_cast<R*>(sp);
     const SmemField<R> s_ro{sm};                    // r on the odd sites
     const SmemField<R> s_rho{sm + 24 * SAP_HALF};   // MR residual (even)
-    const SmemField<R> s_w{sm + 48 * SAP_HALF};     // D_hat rho, later delta_e (even)
-    const SmemField<R> s_t{sm + 72 * SAP_HALF};     // odd temporary
-    R* red = sm + 96 * SAP_HALF;                    // 3 * warps reduction slots
+    const SmemField<R> s_t{sm + 48 * SAP_HALF};     // odd temporary / delta_e at the end
+    R* red = sm + 72 * SAP_HALF;                    // 3 * warps reduction slots
 
     // block of this colour handled by this thread block
     int org[4];
@@ -189,73 +264,93 @@ __global__ void __launch_bounds__(SAP_THREADS) k_sap_block(Geom g, SapGeom sg, i
         org[2] = SAP_BS * b2;
         org[3] = SAP_BS * b3;
     }
-    // this thread's even and odd sites: local pair (2t, 2t+1)
     const int t = threadIdx.x;
     const int base = 2 * t;
     const int par0 = ((base >> 6) + ((base >> 4) & 3) + ((base >> 2) & 3) + (base & 3)) & 1;
     const Site se = make_site(g, org, base + par0);
     const Site so = make_site(g, org, base + 1 - par0);
 
-    // 1. residual r = eta - D psi on both sites
+    if constexpr (BlockLinks<R>::kStaged) {
+        // links and angles of the block's sites, all four directions
+#pragma unroll 1
+        for (int k = 0; k < 2; ++k) {
+            const Site& st_ = k ? so : se;
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    bl.U[(mu * 3 + j) * SAP_SITES + st_.lidx] = f.U[((size_t)mu * 3 + j) * g.V + st_.s];
+            }
+            const float4 a = f.A[st_.s];
+            bl.A[0 * SAP_SITES + st_.lidx] = a.x;
+            bl.A[1 * SAP_SITES + st_.lidx] = a.y;
+            bl.A[2 * SAP_SITES + st_.lidx] = a.z;
+            bl.A[3 * SAP_SITES + st_.lidx] = a.w;
+        }
+    }
+
+    // residual r = eta - D psi on both sites (one call site)
     cplx<R> re[12], v[12], w[12], acc[12];
-    residual_at<R, QNZ>(g, f, eta, q, se, psi_zero, re);
-    residual_at<R, QNZ>(g, f, eta, q, so, psi_zero, v);
+#pragma unroll 1
+    for (int k = 0; k < 2; ++k) {
+        residual_at<R, QNZ>(g, f, eta, q, k ? so : se, psi_zero, k ? v : re);
+    }
     s_ro.store(t, v);
-    // 2. t_o = M_oo^-1 r_o ; rho = r_e - H_eo t_o
-    clover_mul(Cinv, g.V, so.s, v, w);
+    clover_mul(Cinv, g.V, so.s, v, w);  // t_o = M_oo^-1 r_o
     s_t.store(t, w);
     __syncthreads();
-    block_hops<R, QNZ>(g, f, s_t, q, se, acc);
+
     cplx<R> rho[12], de[12];
 #pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        rho[i] = re[i] + R(0.5) * acc[i];
-        de[i] = mk<R>(0, 0);
-    }
-    s_rho.store(t, rho);
-    __syncthreads();
-    // 3. minimal-residual steps on D_hat_B delta_e = rho
-    for (int it = 0; it < nmr; ++it) {
-        // t_o = M_oo^-1 H_oe rho
-        block_hops<R, QNZ>(g, f, s_rho, q, so, acc);
+    for (int i = 0; i < 12; ++i) de[i] = mk<R>(0, 0);
+    const int nsteps = 2 * nmr + 2;
+#pragma unroll 1
+    for (int step = 0; step < nsteps; ++step) {
+        const bool odd = (step & 1) != 0;   // steps 1, 3, ..., 2 nmr + 1 work on the odd sites
+        const bool last = step == nsteps - 1;
+        // odd steps read rho (or delta_e on the last step), even steps read t_o
+        block_hops<R, QNZ>(g, f, bl, odd ? (last ? s_t : s_rho) : s_t, q, odd ? so : se, acc);
+        if (step == 0) {
 #pragma unroll
-        for (int i = 0; i < 12; ++i) v[i] = R(-0.5) * acc[i];
-        clover_mul(Cinv, g.V, so.s, v, w);
-        s_t.store(t, w);
-        __syncthreads();
-        // w_e = M_ee rho - H_eo t_o
-        block_hops<R, QNZ>(g, f, s_t, q, se, acc);
-        clover_mul(f.C, g.V, se.s, rho, w);
+            for (int i = 0; i < 12; ++i) rho[i] = re[i] + R(0.5) * acc[i];
+            s_rho.store(t, rho);
+        } else if (last) {
+            s_ro.load(t, v);
 #pragma unroll
-        for (int i = 0; i < 12; ++i) w[i] = w[i] + R(0.5) * acc[i];
-        R a_re = 0, a_im = 0, b = 0;
+            for (int i = 0; i < 12; ++i) v[i] = v[i] + R(0.5) * acc[i];
+            clover_mul(Cinv, g.V, so.s, v, w);  // delta_o
+        } else if (odd) {
 #pragma unroll
-        for (int i = 0; i < 12; ++i) {
-            a_re += w[i].re * rho[i].re + w[i].im * rho[i].im;
-            a_im += w[i].re * rho[i].im - w[i].im * rho[i].re;
-            b += w[i].re * w[i].re + w[i].im * w[i].im;
+            for (int i = 0; i < 12; ++i) v[i] = R(-0.5) * acc[i];
+            clover_mul(Cinv, g.V, so.s, v, w);
+            s_t.store(t, w);
+        } else {
+            clover_mul(f.C, g.V, se.s, rho, w);
+#pragma unroll
+            for (int i = 0; i < 12; ++i) w[i] = w[i] + R(0.5) * acc[i];
+            R a_re = 0, a_im = 0, b = 0;
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                a_re += w[i].re * rho[i].re + w[i].im * rho[i].im;
+                a_im += w[i].re * rho[i].im - w[i].im * rho[i].re;
+                b += w[i].re * w[i].re + w[i].im * w[i].im;
+            }
+            R sums[3];
+            block_sum3(a_re, a_im, b, red, sums);
+            if (sums[2] > R(0)) {  // else rho = 0 on the whole block: nothing to add
+                const cplx<R> om = mk(sums[0] / sums[2], sums[1] / sums[2]);
+#pragma unroll
+                for (int i = 0; i < 12; ++i) {
+                    de[i] = de[i] + om * rho[i];
+                    rho[i] = rho[i] - om * w[i];
+                }
+            }
+            if (step == nsteps - 2) s_t.store(t, de);  // delta_e for the last step
+            else s_rho.store(t, rho);
         }
-        R sums[3];
-        block_sum3(a_re, a_im, b, red, sums);
-        if (!(sums[2] > R(0))) break;  // rho = 0: converged
-        const cplx<R> om = mk(sums[0] / sums[2], sums[1] / sums[2]);
-#pragma unroll
-        for (int i = 0; i < 12; ++i) {
-            de[i] = de[i] + om * rho[i];
-            rho[i] = rho[i] - om * w[i];
-        }
-        s_rho.store(t, rho);
         __syncthreads();
     }
-    // 4. delta_o = M_oo^-1 (r_o - H_oe delta_e)
-    s_w.store(t, de);
-    __syncthreads();
-    block_hops<R, QNZ>(g, f, s_w, q, so, acc);
-    s_ro.load(t, v);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) v[i] = v[i] + R(0.5) * acc[i];
-    clover_mul(Cinv, g.V, so.s, v, w);
-    // 5. psi_B += delta
+    // psi_B += delta (w holds delta_o)
     typename Fields<R>::vec* psi = const_cast<typename Fields<R>::vec*>(f.psi);
     if (psi_zero) {
         store_spinor(psi, g.V, se.s, de);
@@ -274,7 +369,7 @@ __global__ void __launch_bounds__(SAP_THREADS) k_sap_block(Geom g, SapGeom sg, i
 
 template <typename R>
 size_t sap_smem_bytes() {
-    return (96 * SAP_HALF + 3 * (SAP_THREADS / 32)) * sizeof(R);
+    return sap_link_bytes<R>() + (72 * SAP_HALF + 3 * (SAP_THREADS / 32)) * sizeof(R);
 }
 
 template <typename R, bool QNZ>

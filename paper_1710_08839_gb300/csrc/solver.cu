@@ -75,10 +75,13 @@ void SolverWork::release() {
 }
 
 int SolverWork::ensure(int V_, int nkv_, int prec_) {
-    if (V == V_ && nkv >= nkv_ && prec == prec_) return QXD_OK;
+    // inner vectors are sized for FP64, so switching the inner precision
+    // reuses them; a new lattice size or more Krylov vectors reallocate
+    (void)prec_;
+    if (V == V_ && nkv >= nkv_) return QXD_OK;
     release();
     const size_t b64n = (size_t)V_ * 12 * sizeof(double2);
-    const size_t binn = (size_t)V_ * 12 * (prec_ == QXD_FP32 ? sizeof(float2) : sizeof(double2));
+    const size_t binn = b64n;
     int rc;
     void** full[] = {&b64, &x64, &r64, &t64, &xs, &rs, &ts, &bs, &tmp64};
     for (void** p : full)
@@ -89,7 +92,7 @@ int SolverWork::ensure(int V_, int nkv_, int prec_) {
     if ((rc = red.init())) return rc;
     V = V_;
     nkv = nkv_;
-    prec = prec_;
+    prec = QXD_FP64;
     return QXD_OK;
 }
 
