@@ -89,6 +89,18 @@ int qxd_lattice_create(qxd_lattice** out, int T, int L1, int L2, int L3,
 /* Free all storage of the lattice (NULL is accepted). Synchronises its stream. */
 int qxd_lattice_destroy(qxd_lattice* lat);
 
+/*
+ * A view shares the gauge field (and clover field tensors) of `parent` (or of
+ * parent's own parent) and owns its own quark parameters, clover term,
+ * scratch and solver work: one view per (m0, csw, cswqed, qhat) lets several
+ * quarks use one resident gauge field. Every entry point that takes a
+ * lattice accepts a view, except qxd_set_gauge (QXD_ERR_STATE). A new gauge
+ * field on the parent makes each view's clover term stale: the view returns
+ * QXD_ERR_STATE until it calls qxd_sw_build again. The parent cannot be
+ * destroyed while views exist (QXD_ERR_STATE). stream: NULL = the parent's.
+ */
+int qxd_lattice_view(qxd_lattice** out, qxd_lattice* parent, void* stream);
+
 /* Simulated extents N[4] and volume (number of sites) of the lattice. */
 int qxd_lattice_dims(const qxd_lattice* lat, int* N4, long long* volume);
 
@@ -247,6 +259,57 @@ int qxd_solve(qxd_lattice* lat, void* x, const void* b, const qxd_solver_params*
  *   serialised by the caller.
  */
 int qxd_Dw_noalloc(qxd_lattice* lat, void* out, const void* in, int flags, void* stream);
+
+/*
+ * out[i] = D_i in[i] for i < n in one kernel launch, where D_i is the operator
+ * of lats[i] (lattices or views, possibly of different sizes; the same
+ * lattice may appear many times). Native-layout device buffers, precision
+ * QXD_FP64 or QXD_FP32 in flags. Right-hand sides of one operator share each
+ * site's link, angle and clover loads (rhs_per_site of them per site: 1, 2,
+ * 4 or 8, or 0 to let the library time the choices on the first batch of a
+ * given size class and keep the fastest). Same numbers as qxd_Dw per
+ * right-hand side. The paper applies one operator at a time (Sec. 2.3); this
+ * is the batched form of the same operator.
+ */
+int qxd_Dw_batch(int n, qxd_lattice* const* lats, void* const* out, const void* const* in, int flags,
+                 int rhs_per_site, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched solve engine (continuous batching of independent solves).
+ * Every submitted request is a solve D x = b with its own operator (lattice
+ * or view; views let requests with different m0, qhat share one resident
+ * gauge field). qxd_engine_step advances every active request by one flexible
+ * GCR step (as qxd_solve with system QXD_SOLVE_FULL, inner_prec QXD_FP32),
+ * with one kernel launch per SAP half-cycle, one batched D and one launch
+ * per vector operation for all active requests together; it then retires
+ * finished requests and admits queued ones while the device memory of the
+ * active requests stays within hbm_budget_bytes (a request larger than the
+ * budget runs alone) and their number within max_active. A request's result
+ * does not depend on the other requests in the batch (same kernels, grids
+ * and reduction orders as alone). Work vectors come from the engine's
+ * caching device allocator.
+ * Buffers x and b (FP64, device; lexicographic unless params->flags has
+ * QXD_LAYOUT_NATIVE) and the operator must stay valid until the request is
+ * done (qxd_engine_poll). The paper solves one system at a time; this
+ * engine is a design choice of this library.
+ * ------------------------------------------------------------------------- */
+typedef struct qxd_engine qxd_engine;
+
+int qxd_engine_create(qxd_engine** out, size_t hbm_budget_bytes, int max_active, void* stream);
+int qxd_engine_destroy(qxd_engine* e);
+/* queue a request; id receives its handle */
+int qxd_engine_submit(qxd_engine* e, qxd_lattice* op, void* x, const void* b, const qxd_solver_params* params,
+                      long long* id);
+/* one step for all active requests; counts after the step (n_done: retired by this step) */
+int qxd_engine_step(qxd_engine* e, int* n_active, int* n_pending, int* n_done);
+/* request status; done = 1 once x is written (info.status: QXD_OK, QXD_ERR_NOT_CONVERGED, ...) */
+int qxd_engine_poll(qxd_engine* e, long long id, qxd_solve_info* info, int* done);
+/* drop the record of a finished request */
+int qxd_engine_forget(qxd_engine* e, long long id);
+/* step until no request is active or queued */
+int qxd_engine_run(qxd_engine* e);
+/* device bytes of active requests, bytes held by the allocator, steps so far */
+int qxd_engine_stats(const qxd_engine* e, size_t* bytes_in_use, size_t* bytes_held, long long* steps);
 
 /* Bytes of one spinor field in the native layout for precision `prec`. */
 size_t qxd_spinor_bytes(const qxd_lattice* lat, int prec);

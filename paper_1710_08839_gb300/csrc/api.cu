@@ -42,10 +42,13 @@ static int dalloc(T** p, size_t n, const char* what) {
 }
 
 static void free_all(qxd_lattice* L) {
-    void* ptrs[] = {L->U64, L->U32, L->A64, L->Z64, L->A32, L->ftens, L->C64, L->C32,
-                    L->Cinv64, L->Cinv32, L->d_status, L->scratch_in, L->scratch_out,
-                    L->scratch_lex};
-    for (void* p : ptrs)
+    void* own[] = {L->C64, L->C32, L->Cinv64, L->Cinv32, L->d_status, L->scratch_in, L->scratch_out,
+                   L->scratch_lex};
+    for (void* p : own)
+        if (p) cudaFree(p);
+    if (L->parent) return;  // the gauge field belongs to the parent
+    void* gauge[] = {L->U64, L->U32, L->A64, L->Z64, L->A32, L->ftens};
+    for (void* p : gauge)
         if (p) cudaFree(p);
 }
 
@@ -130,7 +133,11 @@ int qxd_lattice_create(qxd_lattice** out, int T, int L1, int L2, int L3, unsigne
 
 int qxd_lattice_destroy(qxd_lattice* lat) {
     if (!lat) return QXD_OK;
+    if (lat->nviews > 0)
+        return fail(QXD_ERR_STATE, "qxd_lattice_destroy: " + std::to_string(lat->nviews) +
+                                       " views still share this lattice's gauge field");
     cudaStreamSynchronize(lat->stream);
+    if (lat->parent) --lat->parent->nviews;
     release_solver(lat);
     free_all(lat);
     delete lat;
@@ -149,8 +156,46 @@ int qxd_lattice_dims(const qxd_lattice* lat, int* N4, long long* volume) {
     return QXD_OK;
 }
 
+int qxd_lattice_view(qxd_lattice** out, qxd_lattice* parent, void* stream) {
+    if (!out || !parent) return fail(QXD_ERR_ARG, "qxd_lattice_view: NULL argument");
+    *out = nullptr;
+    qxd_lattice* root = gauge_owner(parent);
+    qxd_lattice* v = new (std::nothrow) qxd_lattice();
+    if (!v) return fail(QXD_ERR_OOM, "qxd_lattice_view: host allocation failed");
+    v->g = root->g;
+    v->T = root->T;
+    v->L1 = root->L1;
+    v->L2 = root->L2;
+    v->L3 = root->L3;
+    v->cstar_mask = root->cstar_mask;
+    v->stream = stream ? (cudaStream_t)stream : root->stream;
+    v->device = root->device;
+    v->U64 = root->U64;
+    v->U32 = root->U32;
+    v->A64 = root->A64;
+    v->Z64 = root->Z64;
+    v->A32 = root->A32;
+    v->ftens = root->ftens;
+    v->parent = root;
+    size_t n = (size_t)root->g.V;
+    int rc = 0;
+    if ((rc = dalloc(&v->C64, CLOVER_REALS * n, "cudaMalloc(C64)")) ||
+        (rc = dalloc(&v->C32, CLOVER_F4 * n, "cudaMalloc(C32)")) ||
+        (rc = dalloc(&v->Cinv64, CLOVER_REALS * n, "cudaMalloc(Cinv64)")) ||
+        (rc = dalloc(&v->Cinv32, CLOVER_F4 * n, "cudaMalloc(Cinv32)")) ||
+        (rc = dalloc(&v->d_status, 64, "cudaMalloc(status)"))) {
+        free_all(v);
+        delete v;
+        return rc;
+    }
+    ++root->nviews;
+    *out = v;
+    return QXD_OK;
+}
+
 int qxd_set_gauge(qxd_lattice* lat, const double* su3, const double* u1_angle, int flags) {
     if (!lat || !su3 || !u1_angle) return fail(QXD_ERR_ARG, "qxd_set_gauge: NULL argument");
+    if (lat->parent) return fail(QXD_ERR_STATE, "qxd_set_gauge: a view shares its parent's gauge field");
     int kind = flags & 0x3;
     if (kind == 3 || (flags & ~0x13)) return fail(QXD_ERR_ARG, "qxd_set_gauge: bad flags");
     const bool host = flags & QXD_GAUGE_HOST;
@@ -192,6 +237,7 @@ int qxd_set_gauge(qxd_lattice* lat, const double* su3, const double* u1_angle, i
     if (st[1]) return fail(QXD_ERR_NOT_ADMISSIBLE, "qxd_set_gauge: " + std::to_string(st[1]) +
                                                        " mirror links violate the orbifold constraint");
     lat->has_gauge = true;
+    ++lat->gauge_version;
     return QXD_OK;
 }
 
@@ -210,7 +256,7 @@ int qxd_set_params(qxd_lattice* lat, double m0, double csw, double cswqed, int q
 
 int qxd_sw_build(qxd_lattice* lat) {
     if (!lat) return fail(QXD_ERR_ARG, "qxd_sw_build: lat is NULL");
-    if (!lat->has_gauge || !lat->has_params)
+    if (!gauge_owner(lat)->has_gauge || !lat->has_params)
         return fail(QXD_ERR_STATE, "qxd_sw_build: needs qxd_set_gauge and qxd_set_params first");
     lat->has_clover = false;
     int rc = launch_clover_build(lat, lat->d_status);
@@ -222,6 +268,7 @@ int qxd_sw_build(qxd_lattice* lat) {
     if (st[0]) return fail(QXD_ERR_SW_SINGULAR, "qxd_sw_build: " + std::to_string(st[0]) +
                                                     " clover blocks are singular or not finite");
     lat->has_clover = true;
+    lat->built_gauge_version = gauge_owner(lat)->gauge_version;
     return QXD_OK;
 }
 
@@ -247,7 +294,7 @@ int qxd_spinor_unpack(qxd_lattice* lat, void* lex_out, const void* native_in, in
 int qxd_Dw(qxd_lattice* lat, void* out, const void* in, int flags, void* stream) {
     if (!lat || !out || !in) return fail(QXD_ERR_ARG, "qxd_Dw: NULL argument");
     if (flags & ~(0x1 | 0x10 | 0x100)) return fail(QXD_ERR_ARG, "qxd_Dw: bad flags");
-    if (!lat->has_clover) return fail(QXD_ERR_STATE, "qxd_Dw: needs qxd_sw_build first");
+    if (!qxd::clover_ready(lat)) return fail(QXD_ERR_STATE, "qxd_Dw: needs qxd_sw_build first");
     const int prec = flags & 0x1;
     const bool host = flags & QXD_HOST;
     const bool native = flags & QXD_LAYOUT_NATIVE;

@@ -1,4 +1,6 @@
 // Vector kernels of the Krylov solvers (see blas.cuh).
+#include <new>
+
 #include "blas.cuh"
 
 namespace qxd {
@@ -311,5 +313,181 @@ int blas_f2d(size_t n, const float2* in, double2* out, cudaStream_t st) {
     template int blas_update_x<T>(size_t, int, const CoefList&, const VecList<T>&, double2*, cudaStream_t);
 QXD_BLAS_INST(float2)
 QXD_BLAS_INST(double2)
+
+}  // namespace qxd
+
+namespace qxd {
+
+namespace {
+
+__device__ __forceinline__ void block_reduce_store_at(double* v, int nc, double* __restrict__ partials) {
+    __shared__ double sh[RED_THREADS / 32][2 * BLAS_KMAX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = 0; c < nc; ++c) {
+        double x = v[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[warp][c] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+        double x = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) x += sh[w][threadIdx.x];
+        partials[threadIdx.x] = x;
+    }
+}
+
+// one kernel for all batched operations; the switch is uniform per launch
+__global__ void __launch_bounds__(RED_THREADS) k_blas_batch(int op, const BJob* __restrict__ jobs,
+                                                            double* __restrict__ partials) {
+    const BJob& J = jobs[blockIdx.y];
+    double* part = partials + ((size_t)blockIdx.y * RED_BLOCKS + blockIdx.x) * 2 * BLAS_KMAX;
+    const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t step = (size_t)gridDim.x * blockDim.x;
+    if (op == B_MDOT_F32) {
+        double acc[2 * BLAS_KMAX];
+#pragma unroll
+        for (int c = 0; c < 2 * BLAS_KMAX; ++c) acc[c] = 0.0;
+        const float2* y = (const float2*)J.y;
+        for (size_t i = i0; i < J.n; i += step) {
+            const float2 bv = y[i];
+#pragma unroll
+            for (int j = 0; j < BLAS_KMAX; ++j) {
+                if (j >= J.k) break;
+                const float2 a = ((const float2*)J.xs[j])[i];
+                acc[2 * j] += (double)a.x * bv.x + (double)a.y * bv.y;
+                acc[2 * j + 1] += (double)a.x * bv.y - (double)a.y * bv.x;
+            }
+        }
+        block_reduce_store_at(acc, 2 * J.k, part);
+    } else if (op == B_MAXPY_NORM_F32) {
+        double acc[1] = {0.0};
+        float2* y = (float2*)J.out;
+        for (size_t i = i0; i < J.n; i += step) {
+            double bx = y[i].x, by = y[i].y;
+#pragma unroll
+            for (int j = 0; j < BLAS_KMAX; ++j) {
+                if (j >= J.k) break;
+                const float2 a = ((const float2*)J.xs[j])[i];
+                bx -= J.cre[j] * a.x - J.cim[j] * a.y;
+                by -= J.cre[j] * a.y + J.cim[j] * a.x;
+            }
+            const float2 r = make_float2((float)bx, (float)by);
+            y[i] = r;
+            acc[0] += (double)r.x * r.x + (double)r.y * r.y;
+        }
+        block_reduce_store_at(acc, 1, part);
+    } else if (op == B_NORM2_F64) {
+        double acc[1] = {0.0};
+        const double2* x = (const double2*)J.y;
+        for (size_t i = i0; i < J.n; i += step) acc[0] += x[i].x * x[i].x + x[i].y * x[i].y;
+        block_reduce_store_at(acc, 1, part);
+    } else if (op == B_SUB_NORM_F64) {
+        double acc[1] = {0.0};
+        const double2* b = (const double2*)J.b;
+        const double2* t = (const double2*)J.y;
+        double2* r = (double2*)J.out;
+        for (size_t i = i0; i < J.n; i += step) {
+            const double2 v = make_double2(b[i].x - t[i].x, b[i].y - t[i].y);
+            r[i] = v;
+            acc[0] += v.x * v.x + v.y * v.y;
+        }
+        block_reduce_store_at(acc, 1, part);
+    } else if (op == B_SCALE_F32) {
+        float2* x = (float2*)J.out;
+        for (size_t i = i0; i < J.n; i += step) {
+            const float2 a = x[i];
+            x[i] = make_float2((float)(a.x * J.s), (float)(a.y * J.s));
+        }
+    } else if (op == B_D2F_NATIVE) {
+        const double2* in = (const double2*)J.y;
+        float2* out = (float2*)J.out;
+        const size_t S = J.n;
+        for (size_t s = i0; s < S; s += step) {
+#pragma unroll
+            for (int comp = 0; comp < 12; ++comp) {
+                const double2 v = in[comp * S + s];
+                out[f32_index(S, comp, s)] = make_float2((float)v.x, (float)v.y);
+            }
+        }
+    } else if (op == B_UPDATE_X_NATIVE32) {
+        double2* x = (double2*)J.out;
+        const size_t S = J.n;
+        for (size_t s = i0; s < S; s += step) {
+#pragma unroll
+            for (int comp = 0; comp < 12; ++comp) {
+                double2 bv = x[comp * S + s];
+                const size_t i32 = f32_index(S, comp, s);
+                for (int j = 0; j < J.k; ++j) {
+                    const float2 a = ((const float2*)J.xs[j])[i32];
+                    bv.x += J.cre[j] * a.x - J.cim[j] * a.y;
+                    bv.y += J.cre[j] * a.y + J.cim[j] * a.x;
+                }
+                x[comp * S + s] = bv;
+            }
+        }
+    }
+}
+
+__global__ void k_reduce_final_batch(const double* __restrict__ partials, int nc, double* __restrict__ res) {
+    const int c = threadIdx.x;
+    if (c >= nc) return;
+    const double* p = partials + (size_t)blockIdx.x * RED_BLOCKS * 2 * BLAS_KMAX;
+    double x = 0.0;
+    for (int b = 0; b < RED_BLOCKS; ++b) x += p[(size_t)b * 2 * BLAS_KMAX + c];
+    res[(size_t)blockIdx.x * 2 * BLAS_KMAX + c] = x;
+}
+
+}  // namespace
+
+int BatchReducer::ensure(int jobs) {
+    if (jobs <= cap) return QXD_OK;
+    release();
+    const int c = jobs < 16 ? 16 : jobs;
+    QXD_CUDA(cudaMalloc(&partials, sizeof(double) * (size_t)c * RED_BLOCKS * 2 * BLAS_KMAX));
+    QXD_CUDA(cudaMalloc(&d_res, sizeof(double) * (size_t)c * 2 * BLAS_KMAX));
+    QXD_CUDA(cudaMallocHost(&h_res, sizeof(double) * (size_t)c * 2 * BLAS_KMAX));
+    QXD_CUDA(cudaMalloc(&d_jobs, sizeof(BJob) * (size_t)c));
+    // pageable on purpose: a copy from pageable memory returns once the data
+    // is staged, so the table can be refilled right after a launch
+    h_jobs = new (std::nothrow) BJob[c];
+    if (!h_jobs) return fail(QXD_ERR_OOM, "batched BLAS: host allocation failed");
+    cap = c;
+    return QXD_OK;
+}
+
+void BatchReducer::release() {
+    if (partials) cudaFree(partials);
+    if (d_res) cudaFree(d_res);
+    if (h_res) cudaFreeHost(h_res);
+    if (d_jobs) cudaFree(d_jobs);
+    delete[] h_jobs;
+    partials = d_res = h_res = nullptr;
+    d_jobs = h_jobs = nullptr;
+    cap = 0;
+}
+
+int blas_batch(BatchReducer& red, BOp op, int jobs, int nc, cudaStream_t st) {
+    if (jobs <= 0) return QXD_OK;
+    QXD_CUDA(cudaMemcpyAsync(red.d_jobs, red.h_jobs, sizeof(BJob) * (size_t)jobs, cudaMemcpyHostToDevice, st));
+    const bool reduce = op == B_MDOT_F32 || op == B_MAXPY_NORM_F32 || op == B_NORM2_F64 || op == B_SUB_NORM_F64;
+    // the elementwise kernels of the single-job path use ew_blocks(n); the
+    // reductions use RED_BLOCKS: keep the same grid per job
+    dim3 grid(RED_BLOCKS, jobs);
+    if (!reduce) {
+        size_t nmax = 0;
+        for (int j = 0; j < jobs; ++j) nmax = nmax > red.h_jobs[j].n ? nmax : red.h_jobs[j].n;
+        grid.x = ew_blocks(nmax);
+    }
+    k_blas_batch<<<grid, RED_THREADS, 0, st>>>((int)op, red.d_jobs, red.partials);
+    QXD_LAUNCHED("k_blas_batch");
+    if (!reduce) return QXD_OK;
+    k_reduce_final_batch<<<jobs, 2 * BLAS_KMAX, 0, st>>>(red.partials, nc, red.d_res);
+    QXD_LAUNCHED("k_reduce_final_batch");
+    QXD_CUDA(cudaMemcpyAsync(red.h_res, red.d_res, sizeof(double) * (size_t)jobs * 2 * BLAS_KMAX,
+                             cudaMemcpyDeviceToHost, st));
+    QXD_CUDA(cudaStreamSynchronize(st));
+    return QXD_OK;
+}
 
 }  // namespace qxd

@@ -67,3 +67,41 @@ int blas_d2f(size_t n, const double2* in, float2* out, cudaStream_t st);
 int blas_f2d(size_t n, const float2* in, double2* out, cudaStream_t st);
 
 }  // namespace qxd
+
+namespace qxd {
+
+// ---------------------------------------------------------------------------
+// Batched forms: one launch serves many independent jobs (grid.y = job). Each
+// job's reduction uses exactly the grid and order of the single-job kernel,
+// so a job's numbers do not depend on which other jobs share the launch.
+// ---------------------------------------------------------------------------
+struct BJob {
+    size_t n;              // complex numbers (or sites S for the native kernels)
+    int k;                 // vectors in xs
+    const void* xs[BLAS_KMAX];
+    const void* y;         // read operand
+    void* out;             // written operand
+    const void* b;         // extra operand (sub_norm)
+    double cre[BLAS_KMAX], cim[BLAS_KMAX];
+    double s;              // scale
+};
+
+struct BatchReducer {
+    double* partials = nullptr;  // [jobs][RED_BLOCKS][2 KMAX]
+    double* d_res = nullptr;     // [jobs][2 KMAX]
+    double* h_res = nullptr;     // pinned
+    BJob* d_jobs = nullptr;
+    BJob* h_jobs = nullptr;      // host copy of the job table (pageable)
+    int cap = 0;
+    int ensure(int jobs);
+    void release();
+};
+
+enum BOp { B_MDOT_F32, B_MAXPY_NORM_F32, B_SCALE_F32, B_NORM2_F64, B_SUB_NORM_F64, B_D2F_NATIVE,
+           B_UPDATE_X_NATIVE32 };
+
+// run op on the first `jobs` entries of red.h_jobs; reductions return nc
+// values per job in red.h_res[job * 2 KMAX + c] (synchronises the stream)
+int blas_batch(BatchReducer& red, BOp op, int jobs, int nc, cudaStream_t st);
+
+}  // namespace qxd

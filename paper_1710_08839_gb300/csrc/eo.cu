@@ -171,7 +171,7 @@ int eo_api(qxd_lattice* lat, int what, void* out, const void* in, int flags, voi
     if (flags & ~(0x1 | 0x100)) return fail(QXD_ERR_ARG, std::string(name) + ": bad flags (device buffers only)");
     if (what != EOAPI_RECONSTRUCT && out == in)
         return fail(QXD_ERR_ARG, std::string(name) + ": in and out must not overlap");
-    if (!lat->has_clover) return fail(QXD_ERR_STATE, std::string(name) + ": needs qxd_sw_build first");
+    if (!qxd::clover_ready(lat)) return fail(QXD_ERR_STATE, std::string(name) + ": needs qxd_sw_build first");
     const int prec = flags & 0x1;
     cudaStream_t st = stream ? (cudaStream_t)stream : lat->stream;
     int rc = ensure_scratch(lat);

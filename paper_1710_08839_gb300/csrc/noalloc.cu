@@ -73,7 +73,7 @@ extern "C" int qxd_Dw_noalloc(qxd_lattice* lat, void* out, const void* in, int f
     if (flags & ~0x1)
         return fail(QXD_ERR_ARG, "qxd_Dw_noalloc: only QXD_FP64 or QXD_FP32 (device buffers, lexicographic layout)");
     if (out == in) return fail(QXD_ERR_ARG, "qxd_Dw_noalloc: in and out must not overlap");
-    if (!lat->has_clover) return fail(QXD_ERR_STATE, "qxd_Dw_noalloc: needs qxd_sw_build first");
+    if (!qxd::clover_ready(lat)) return fail(QXD_ERR_STATE, "qxd_Dw_noalloc: needs qxd_sw_build first");
     if ((long long)lat->g.V > kNoAllocMaxSites)
         return fail(QXD_ERR_ARG, "qxd_Dw_noalloc: lattice has " + std::to_string(lat->g.V) +
                                      " sites, the fixed scratch serves at most " +

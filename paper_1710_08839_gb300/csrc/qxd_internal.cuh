@@ -248,6 +248,13 @@ struct qxd_lattice {
     void* scratch_lex = nullptr;  // lexicographic FP64 spinor
 
     qxd::SolverWork* solver = nullptr;  // Krylov work vectors (first solve)
+
+    // views: a view shares the gauge field of its parent and owns its own
+    // parameters, clover term, scratch and solver work
+    qxd_lattice* parent = nullptr;
+    int nviews = 0;                    // live views of this lattice
+    unsigned gauge_version = 0;        // bumped by every successful set_gauge
+    unsigned built_gauge_version = 0;  // gauge version the clover was built from
 };
 
 namespace qxd {
@@ -260,5 +267,12 @@ int launch_dirac(qxd_lattice* lat, void* out, const void* in, int prec, cudaStre
 int launch_pack(qxd_lattice* lat, void* nat, const void* lex, int prec, cudaStream_t st);
 int launch_unpack(qxd_lattice* lat, void* lex, const void* nat, int prec, cudaStream_t st);
 int ensure_scratch(qxd_lattice* lat);
+// the lattice that owns the gauge field (the lattice itself unless a view)
+inline qxd_lattice* gauge_owner(qxd_lattice* lat) { return lat->parent ? lat->parent : lat; }
+inline const qxd_lattice* gauge_owner(const qxd_lattice* lat) { return lat->parent ? lat->parent : lat; }
+// clover built and still matching the current gauge field
+inline bool clover_ready(const qxd_lattice* lat) {
+    return lat->has_clover && lat->built_gauge_version == gauge_owner(lat)->gauge_version;
+}
 void release_solver(qxd_lattice* lat);
 }  // namespace qxd

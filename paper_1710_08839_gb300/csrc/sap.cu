@@ -14,6 +14,8 @@
 // Starting from psi = 0, ncy cycles give psi = SAP(eta).
 // The block spinors live in shared memory; links and clover blocks are read
 // from the global fields.
+#include <vector>
+
 #include "dirac_common.cuh"
 #include "solver.cuh"
 
@@ -51,8 +53,8 @@ struct BlockLinks;
 template <>
 struct BlockLinks<float> {
     static constexpr bool kStaged = true;
-    float4* U;  // [4][3][256] by local site index
-    float* A;   // [4][256]
+    float4* U;   // [4][3][256] by local site index
+    float2* Z;   // [4][256] z^qhat = exp(i qhat A), computed once per block visit
     __device__ __forceinline__ void link(const Fields<float>&, const Geom&, int mu, int lidx, int,
                                          cplx<float> u[3][3]) const {
         const float4 a = U[(mu * 3 + 0) * SAP_SITES + lidx];
@@ -69,13 +71,9 @@ struct BlockLinks<float> {
         u[2][2] = conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
     }
     __device__ __forceinline__ cplx<float> phase(const Fields<float>&, const Geom&, int mu, int lidx, int,
-                                                 float q) const {
-        float t = q * A[mu * SAP_SITES + lidx];
-        const float k = rintf(t * 0.15915494309189535f);
-        t = fmaf(-k, 6.2831853071795865f, t);
-        float sn, cs;
-        __sincosf(t, &sn, &cs);
-        return mk(cs, sn);
+                                                 float) const {
+        const float2 z = Z[mu * SAP_SITES + lidx];
+        return mk(z.x, z.y);
     }
 };
 
@@ -158,7 +156,7 @@ __device__ __forceinline__ void block_dir(const Geom& g, const Fields<R>& f, con
 }
 
 template <typename R, bool QNZ>
-__device__ __noinline__ void block_hops(const Geom& g, const Fields<R>& f, const BlockLinks<R>& bl,
+__device__ __forceinline__ void block_hops(const Geom& g, const Fields<R>& f, const BlockLinks<R>& bl,
                                         const SmemField<R> src, R q, const Site& t, cplx<R> acc[12]) {
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = mk<R>(0, 0);
@@ -217,7 +215,7 @@ __device__ __forceinline__ void block_sum3(R a, R b, R c, R* red, R out[3]) {
 
 template <typename R>
 constexpr size_t sap_link_bytes() {
-    return BlockLinks<R>::kStaged ? (12 * SAP_SITES * sizeof(float4) + 4 * SAP_SITES * sizeof(float)) : 0;
+    return BlockLinks<R>::kStaged ? (12 * SAP_SITES * sizeof(float4) + 4 * SAP_SITES * sizeof(float2)) : 0;
 }
 
 // Each thread owns one even and one odd site of the block: the local pair
@@ -230,16 +228,15 @@ constexpr size_t sap_link_bytes() {
 //                      rho -= omega w (even)             for k < nmr
 //   last step:         delta_o = M_oo^-1 (r_o - H_oe delta_e)     (odd)
 template <typename R, bool QNZ>
-__global__ void __launch_bounds__(SAP_THREADS, 2) k_sap_block(Geom g, SapGeom sg, int colour, int psi_zero,
-                                                              Fields<R> f, const typename Fields<R>::cvec* __restrict__ Cinv,
-                                                              const typename Fields<R>::vec* __restrict__ eta, int nmr,
-                                                              R q) {
+__device__ __forceinline__ void sap_block_body(const Geom& g, const SapGeom& sg, int bidx, int colour, int psi_zero,
+                                               const Fields<R>& f, const typename Fields<R>::cvec* __restrict__ Cinv,
+                                               const typename Fields<R>::vec* __restrict__ eta, int nmr, R q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BlockLinks<R> bl;
     unsigned char* sp = smem_raw;
     if constexpr (BlockLinks<R>::kStaged) {
         bl.U = reinterpret_cast<float4*>(sp);
-        bl.A = reinterpret_cast<float*>(sp + 12 * SAP_SITES * sizeof(float4));
+        bl.Z = reinterpret_cast<float2*>(sp + 12 * SAP_SITES * sizeof(float4));
         sp += sap_link_bytes<R>();
     }
     R* sm = reinterpret_cast<R*>(sp);
@@ -251,7 +248,7 @@ __global__ void __launch_bounds__(SAP_THREADS, 2) k_sap_block(Geom g, SapGeom sg
     // block of this colour handled by this thread block
     int org[4];
     {
-        const int bi2 = 2 * blockIdx.x;
+        const int bi2 = 2 * bidx;
         const int b3e = bi2 % sg.nb3;
         int rest = bi2 / sg.nb3;
         const int b2 = rest % sg.nb2;
@@ -281,11 +278,11 @@ __global__ void __launch_bounds__(SAP_THREADS, 2) k_sap_block(Geom g, SapGeom sg
                 for (int j = 0; j < 3; ++j)
                     bl.U[(mu * 3 + j) * SAP_SITES + st_.lidx] = f.U[((size_t)mu * 3 + j) * g.V + st_.s];
             }
-            const float4 a = f.A[st_.s];
-            bl.A[0 * SAP_SITES + st_.lidx] = a.x;
-            bl.A[1 * SAP_SITES + st_.lidx] = a.y;
-            bl.A[2 * SAP_SITES + st_.lidx] = a.z;
-            bl.A[3 * SAP_SITES + st_.lidx] = a.w;
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+                const cplx<float> z = QNZ ? link_phase(f.A, g.V, mu, st_.s, q) : mk(1.f, 0.f);
+                bl.Z[mu * SAP_SITES + st_.lidx] = make_float2(z.re, z.im);
+            }
         }
     }
 
@@ -367,6 +364,29 @@ __global__ void __launch_bounds__(SAP_THREADS, 2) k_sap_block(Geom g, SapGeom sg
     }
 }
 
+template <typename R, bool QNZ>
+__global__ void __launch_bounds__(SAP_THREADS, 2) k_sap_block(Geom g, SapGeom sg, int colour, int psi_zero,
+                                                              Fields<R> f, const typename Fields<R>::cvec* __restrict__ Cinv,
+                                                              const typename Fields<R>::vec* __restrict__ eta, int nmr,
+                                                              R q) {
+    sap_block_body<R, QNZ>(g, sg, blockIdx.x, colour, psi_zero, f, Cinv, eta, nmr, q);
+}
+
+// batched form: thread block b works on block (b - cta_begin) of the job
+// whose range holds b (one launch serves every job of a batch)
+__global__ void __launch_bounds__(SAP_THREADS, 2) k_sap_block_batch(const SapJob* __restrict__ jobs, int njobs,
+                                                                    int colour, int psi_zero, int nmr) {
+    int lo = 0, hi = njobs - 1;
+    const int b = blockIdx.x;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].cta_begin <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const SapJob& J = jobs[lo];
+    sap_block_body<float, true>(J.g, J.sg, b - J.cta_begin, colour, psi_zero, J.f, J.Cinv, J.eta, nmr, J.q);
+}
+
 template <typename R>
 size_t sap_smem_bytes() {
     return sap_link_bytes<R>() + (72 * SAP_HALF + 3 * (SAP_THREADS / 32)) * sizeof(R);
@@ -446,6 +466,37 @@ int sap_apply(qxd_lattice* lat, SapWork& w, void* out, const void* in, int ncy, 
 }
 
 template int sap_apply<float>(qxd_lattice*, SapWork&, void*, const void*, int, int, cudaStream_t);
+
+SapGeom sap_geom(const Geom& g) {
+    SapGeom sg;
+    sg.nb0 = g.N0 / SAP_BS;
+    sg.nb1 = g.N1 / SAP_BS;
+    sg.nb2 = g.N2 / SAP_BS;
+    sg.nb3 = g.N3 / SAP_BS;
+    sg.nblk = sg.nb0 * sg.nb1 * sg.nb2 * sg.nb3;
+    sg.nhalf = sg.nblk / 2;
+    return sg;
+}
+
+int sap_apply_batch(std::vector<SapJob>& jobs, SapJob* d_jobs, int ncy, int nmr, cudaStream_t st) {
+    if (jobs.empty()) return QXD_OK;
+    int ctas = 0;
+    for (auto& J : jobs) {
+        J.cta_begin = ctas;
+        ctas += J.sg.nhalf;
+        QXD_CUDA(cudaMemsetAsync((void*)J.f.psi, 0, (size_t)J.g.V * 24 * sizeof(float), st));
+    }
+    QXD_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(SapJob), cudaMemcpyHostToDevice, st));
+    const size_t smem = sap_smem_bytes<float>();
+    QXD_CUDA(cudaFuncSetAttribute(k_sap_block_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int cy = 0; cy < ncy; ++cy)
+        for (int colour = 0; colour < 2; ++colour) {
+            const int psi_zero = (cy == 0 && colour == 0) ? 1 : 0;
+            k_sap_block_batch<<<ctas, SAP_THREADS, smem, st>>>(d_jobs, (int)jobs.size(), colour, psi_zero, nmr);
+            QXD_LAUNCHED("k_sap_block_batch");
+        }
+    return QXD_OK;
+}
 template int sap_apply<double>(qxd_lattice*, SapWork&, void*, const void*, int, int, cudaStream_t);
 
 }  // namespace qxd
@@ -457,7 +508,7 @@ extern "C" int qxd_sap(qxd_lattice* lat, void* out, const void* in, int ncy, int
     if (flags & ~(0x1 | 0x100)) return fail(QXD_ERR_ARG, "qxd_sap: bad flags (device buffers only)");
     if (ncy < 1 || nmr < 1) return fail(QXD_ERR_ARG, "qxd_sap: ncy and nmr must be >= 1");
     if (out == in) return fail(QXD_ERR_ARG, "qxd_sap: in and out must not overlap");
-    if (!lat->has_clover) return fail(QXD_ERR_STATE, "qxd_sap: needs qxd_sw_build first");
+    if (!qxd::clover_ready(lat)) return fail(QXD_ERR_STATE, "qxd_sap: needs qxd_sw_build first");
     int rc = sap_check(lat);
     if (rc) return rc;
     const int prec = flags & 0x1;

@@ -332,7 +332,7 @@ int qxd_solve(qxd_lattice* lat, void* x, const void* b, const qxd_solver_params*
         return fail(QXD_ERR_ARG, "qxd_solve: sap_ncy and sap_nmr must be >= 1");
     if ((P.flags & QXD_HOST) && (P.flags & QXD_LAYOUT_NATIVE))
         return fail(QXD_ERR_ARG, "qxd_solve: host buffers must use the lexicographic layout");
-    if (!lat->has_clover) return fail(QXD_ERR_STATE, "qxd_solve: needs qxd_sw_build first");
+    if (!qxd::clover_ready(lat)) return fail(QXD_ERR_STATE, "qxd_solve: needs qxd_sw_build first");
     cudaStream_t st = stream ? (cudaStream_t)stream : lat->stream;
     int rc;
     if (P.precond == QXD_PRECOND_SAP && (rc = sap_check(lat))) return rc;

@@ -1,7 +1,10 @@
 // Solver workspace and the Schwarz (SAP) preconditioner interface.
 #pragma once
 
+#include <vector>
+
 #include "blas.cuh"
+#include "dirac_common.cuh"
 #include "qxd_internal.cuh"
 
 namespace qxd {
@@ -17,6 +20,22 @@ struct SapGeom {
 struct SapWork {
     SapGeom sg{};
 };
+
+// one job of a batched SAP application (FP32): out = SAP(eta) on the job's
+// operator; f.psi is the output field
+struct SapJob {
+    Geom g;
+    SapGeom sg;
+    Fields<float> f;
+    const float4* Cinv;
+    const float4* eta;
+    float q;
+    int cta_begin;
+};
+SapGeom sap_geom(const Geom& g);
+// every job's SAP in one launch per half-cycle; d_jobs: device table with
+// room for jobs.size() entries
+int sap_apply_batch(std::vector<SapJob>& jobs, SapJob* d_jobs, int ncy, int nmr, cudaStream_t st);
 
 struct SolverWork {
     int V = 0, nkv = 0, prec = -1;

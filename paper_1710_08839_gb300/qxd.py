@@ -75,18 +75,30 @@ class qxd_solve_info(ctypes.Structure):
 SIGNATURES = {
     "qxd_lattice_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, ctypes.c_uint, _vp]),
     "qxd_lattice_destroy": (_i, [_vp]),
+    "qxd_lattice_view": (_i, [ctypes.POINTER(_vp), _vp, _vp]),
     "qxd_lattice_dims": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_longlong)]),
     "qxd_set_gauge": (_i, [_vp, _vp, _vp, _i]),
     "qxd_set_params": (_i, [_vp, _d, _d, _d, _i]),
     "qxd_sw_build": (_i, [_vp]),
     "qxd_Dw": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_Dw_noalloc": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "qxd_Dw_batch": (_i, [_i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _vp]),
     "qxd_Dhat": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_eo_prepare": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_eo_reconstruct": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_sap": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "qxd_solver_defaults": (None, [ctypes.POINTER(qxd_solver_params)]),
     "qxd_solve": (_i, [_vp, _vp, _vp, ctypes.POINTER(qxd_solver_params), ctypes.POINTER(qxd_solve_info), _vp]),
+    "qxd_engine_create": (_i, [ctypes.POINTER(_vp), ctypes.c_size_t, _i, _vp]),
+    "qxd_engine_destroy": (_i, [_vp]),
+    "qxd_engine_submit": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(qxd_solver_params),
+                               ctypes.POINTER(ctypes.c_longlong)]),
+    "qxd_engine_step": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "qxd_engine_poll": (_i, [_vp, ctypes.c_longlong, ctypes.POINTER(qxd_solve_info), ctypes.POINTER(_i)]),
+    "qxd_engine_forget": (_i, [_vp, ctypes.c_longlong]),
+    "qxd_engine_run": (_i, [_vp]),
+    "qxd_engine_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                              ctypes.POINTER(ctypes.c_longlong)]),
     "qxd_spinor_bytes": (ctypes.c_size_t, [_vp, _i]),
     "qxd_spinor_pack": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_spinor_unpack": (_i, [_vp, _vp, _vp, _i, _vp]),
@@ -191,6 +203,14 @@ def qxd_solve(lat, x_ptr, b_ptr, params: qxd_solver_params, stream=0):
     return rc, info
 
 
+def qxd_Dw_batch(lats, outs, ins, prec, rhs_per_site=0, stream=0) -> int:
+    """lats, outs, ins: equal-length sequences of lattice handles and native
+    device buffer pointers."""
+    n = len(lats)
+    arr = lambda xs: (_vp * max(n, 1))(*xs)
+    return check(_call("qxd_Dw_batch", n, arr(lats), arr(outs), arr(ins), prec, rhs_per_site, stream))
+
+
 def qxd_last_error() -> str:
     return lib().qxd_last_error().decode()
 
@@ -228,15 +248,25 @@ class Lattice:
     ``spinor_bytes(prec)`` bytes.
     """
 
-    def __init__(self, T, L1, L2, L3, cstar_mask=0b1110, stream=None):
+    def __init__(self, T, L1, L2, L3, cstar_mask=0b1110, stream=None, parent=None):
         self.T, self.L1, self.L2, self.L3 = T, L1, L2, L3
         self.cstar_mask = cstar_mask
-        self.handle = qxd_lattice_create(T, L1, L2, L3, cstar_mask, _stream_ptr(stream))
+        self.parent = parent
+        if parent is None:
+            self.handle = qxd_lattice_create(T, L1, L2, L3, cstar_mask, _stream_ptr(stream))
+        else:
+            h = _vp()
+            check(_call("qxd_lattice_view", ctypes.byref(h), parent.handle, _stream_ptr(stream)))
+            self.handle = h.value
         N = (_i * 4)()
         V = ctypes.c_longlong()
         check(_call("qxd_lattice_dims", self.handle, N, ctypes.byref(V)))
         self.N = tuple(N)
         self.V = V.value
+
+    def view(self, stream=None) -> "Lattice":
+        """A lattice sharing this one's gauge field, with its own parameters."""
+        return Lattice(self.T, self.L1, self.L2, self.L3, self.cstar_mask, stream=stream, parent=self)
 
     def close(self):
         if self.handle:
@@ -332,3 +362,63 @@ class Lattice:
     def unpack(self, lex_out, native_in, prec, stream=None):
         qxd_spinor_unpack(self.handle, lex_out.data_ptr(), native_in.data_ptr(), prec, _stream_ptr(stream))
         return lex_out
+
+
+class Engine:
+    """Batched solve engine (qxd_engine_*): submit requests, step, poll."""
+
+    def __init__(self, hbm_budget_bytes, max_active=64, stream=None):
+        h = _vp()
+        check(_call("qxd_engine_create", ctypes.byref(h), int(hbm_budget_bytes), int(max_active),
+                    _stream_ptr(stream)))
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, op: "Lattice", x, b, **kw) -> int:
+        p = qxd_solver_defaults()
+        p.precond = QXD_PRECOND_SAP
+        p.inner_prec = QXD_FP32
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown solver parameter {k}")
+            setattr(p, k, v)
+        rid = ctypes.c_longlong()
+        check(_call("qxd_engine_submit", self.handle, op.handle, x.data_ptr(), b.data_ptr(), ctypes.byref(p),
+                    ctypes.byref(rid)))
+        self._keep[rid.value] = (op, x, b)
+        return rid.value
+
+    def step(self):
+        a, pnd, d = _i(), _i(), _i()
+        check(_call("qxd_engine_step", self.handle, ctypes.byref(a), ctypes.byref(pnd), ctypes.byref(d)))
+        return a.value, pnd.value, d.value
+
+    def poll(self, rid):
+        info = qxd_solve_info()
+        done = _i()
+        check(_call("qxd_engine_poll", self.handle, ctypes.c_longlong(rid), ctypes.byref(info), ctypes.byref(done)))
+        return bool(done.value), info.as_dict()
+
+    def forget(self, rid):
+        check(_call("qxd_engine_forget", self.handle, ctypes.c_longlong(rid)))
+        self._keep.pop(rid, None)
+
+    def run(self):
+        check(_call("qxd_engine_run", self.handle))
+
+    def stats(self):
+        a, h, s = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_longlong()
+        check(_call("qxd_engine_stats", self.handle, ctypes.byref(a), ctypes.byref(h), ctypes.byref(s)))
+        return {"bytes_in_use": a.value, "bytes_held": h.value, "steps": s.value}
+
+    def close(self):
+        if self.handle:
+            check(_call("qxd_engine_destroy", self.handle))
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,193 @@
+"""Views (several quarks on one resident gauge field), the batched
+multi-right-hand-side D over operators of different lattice sizes, and the
+batched solve engine (continuous batching), on the GPU."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from qxd_cases import Case, rel_max, rel_norm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as ge
+    ge.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def native(lat, x, prec):
+    n = torch.empty(lat.spinor_bytes(prec), dtype=torch.uint8, device="cuda")
+    lat.pack(n, x, prec)
+    return n
+
+
+def test_views_share_the_gauge_field():
+    from paper_1710_08839_gb300 import qxd
+    c = Case(T=8, L1=4, L2=4, L3=4, qhat=2)
+    parent = c.lattice()
+    params = [(0.05, 1.0, 1.0, -1), (0.2, 1.3, 0.7, 2), (0.1, 1.0, 1.0, 0)]
+    views = []
+    for m0, csw, cq, q in params:
+        v = parent.view()
+        v.set_params(m0, csw, cq, q)
+        v.sw_build()
+        views.append(v)
+    x = c.psi.cuda()
+    for (m0, csw, cq, q), v in zip(params, views):
+        y = torch.empty_like(x)
+        v.Dw(y, x)
+        c2 = Case(T=8, L1=4, L2=4, L3=4, m0=m0, csw=csw, cswqed=cq, qhat=q)
+        ref = c2.oracle(c.su3, c.ang).apply(c.psi.numpy())
+        assert rel_max(y.cpu().numpy(), ref) < 1e-13
+    with pytest.raises(qxd.QxdError) as e:
+        views[0].set_gauge(c.su3.cuda(), c.ang.cuda())
+    assert e.value.code == qxd.QXD_ERR_STATE
+    with pytest.raises(qxd.QxdError) as e:
+        parent.close()
+    assert e.value.code == qxd.QXD_ERR_STATE
+    # a new gauge field on the parent makes the views stale until sw_build
+    parent.set_gauge(c.su3.cuda(), c.ang.cuda())
+    with pytest.raises(qxd.QxdError) as e:
+        views[0].Dw(torch.empty_like(x), x)
+    assert e.value.code == qxd.QXD_ERR_STATE
+    views[0].sw_build()
+    views[0].Dw(torch.empty_like(x), x)
+    for v in views:
+        v.close()
+    parent.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("nr", [0, 1, 2, 4, 8])
+def test_batched_dw_matches_single(prec, nr):
+    from paper_1710_08839_gb300 import qxd
+    p = qxd.QXD_FP64 if prec == "fp64" else qxd.QXD_FP32
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    small = Case(T=8, L1=4, L2=4, L3=4, qhat=2)
+    big = Case(T=8, L1=8, L2=8, L3=8, qhat=-1, seed=3)   # different size
+    lats, ops = [], []
+    for c in (small, big):
+        par = c.lattice()
+        lats.append(par)
+        for m0, q in ((0.05, -1), (0.1, 2)):
+            v = par.view()
+            v.set_params(m0, 1.0, 1.0, q)
+            v.sw_build()
+            ops.append((c, v))
+    rng = np.random.default_rng(9)
+    handles, ins, outs, refs = [], [], [], []
+    for c, v in ops:
+        for r in range(3):
+            src = torch.from_numpy(rng.normal(size=(c.V, 4, 3)) + 1j * rng.normal(size=(c.V, 4, 3))).to(dt).cuda()
+            xn = native(v, src, p)
+            yn = torch.empty_like(xn)
+            y = torch.empty_like(src)
+            v.Dw(y, src)
+            handles.append(v.handle)
+            ins.append(xn)
+            outs.append(yn)
+            refs.append((v, y))
+    qxd.qxd_Dw_batch(handles, [o.data_ptr() for o in outs], [i.data_ptr() for i in ins], p, nr,
+                     torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    for (v, y), yn in zip(refs, outs):
+        got = torch.empty_like(y)
+        v.unpack(got, yn, p)
+        a, b = got.cpu().numpy().astype(np.complex128), y.cpu().numpy().astype(np.complex128)
+        assert (rel_max(a, b) < 1e-13) if prec == "fp64" else (rel_norm(a, b) < 1e-6)
+    for _, v in ops:
+        v.close()
+    for l in lats:
+        l.close()
+
+
+def _engine_setup():
+    # two lattices that admit the 4^4 SAP blocks, two quarks on each
+    a = Case(T=8, L1=8, L2=8, L3=8, qhat=2)
+    b = Case(T=16, L1=8, L2=8, L3=8, qhat=-1, seed=5)
+    pa, pb = a.lattice(), b.lattice()
+    reqs = []
+    rng = np.random.default_rng(13)
+    for c, par in ((a, pa), (b, pb)):
+        for m0, q in ((0.05, -1), (0.1, 2)):
+            v = par.view()
+            v.set_params(m0, 1.0, 1.0, q)
+            v.sw_build()
+            bsrc = torch.from_numpy(rng.normal(size=(c.V, 4, 3)) + 1j * rng.normal(size=(c.V, 4, 3))).cuda()
+            reqs.append((c, v, bsrc))
+    return (pa, pb), reqs
+
+
+def test_engine_results_same_alone_and_in_mix():
+    from paper_1710_08839_gb300 import qxd
+    parents, reqs = _engine_setup()
+    # all requests together
+    eng = qxd.Engine(hbm_budget_bytes=64 << 30, max_active=16)
+    xs_mix = [torch.zeros_like(b) for _, _, b in reqs]
+    ids = [eng.submit(v, x, b, tol=1e-10) for (_, v, b), x in zip(reqs, xs_mix)]
+    eng.run()
+    infos = []
+    for rid in ids:
+        done, info = eng.poll(rid)
+        assert done and info["status"] == qxd.QXD_OK, info
+        assert info["true_relres"] <= 1e-10
+        infos.append(info)
+    eng.close()
+    # each alone, in a fresh engine
+    for (c, v, b), xm in zip(reqs, xs_mix):
+        e1 = qxd.Engine(hbm_budget_bytes=64 << 30, max_active=16)
+        x1 = torch.zeros_like(b)
+        rid = e1.submit(v, x1, b, tol=1e-10)
+        e1.run()
+        assert e1.poll(rid)[0]
+        e1.close()
+        torch.cuda.synchronize()
+        assert torch.equal(x1, xm)
+    # the true residual with the oracle's D on the smaller lattice
+    c, v, b = reqs[0]
+    op = O.Dirac(O.Lattice(c.T, c.L1, c.L2, c.L3, c.mask),
+                 O.GaugeField.from_physical(O.Lattice(c.T, c.L1, c.L2, c.L3, c.mask), c.su3.numpy(), c.ang.numpy()),
+                 0.05, 1.0, 1.0, -1)
+    bb = b.cpu().numpy()
+    r = bb - op.apply(xs_mix[0].cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(bb) < 2e-10
+    for _, v, _ in reqs:
+        v.close()
+    for p in parents:
+        p.close()
+
+
+def test_engine_admission_by_budget_and_agreement_with_solve():
+    from paper_1710_08839_gb300 import qxd
+    parents, reqs = _engine_setup()
+    c, v, b = reqs[0]
+    # budget below one request: requests run one at a time, all complete
+    eng = qxd.Engine(hbm_budget_bytes=1 << 20, max_active=16)
+    xs = [torch.zeros_like(bb) for _, _, bb in reqs]
+    ids = [eng.submit(vv, x, bb, tol=1e-10) for (_, vv, bb), x in zip(reqs, xs)]
+    max_active = 0
+    while True:
+        a, p, d = eng.step()
+        max_active = max(max_active, a)
+        if a == 0 and p == 0:
+            break
+    assert max_active == 1
+    for rid in ids:
+        done, info = eng.poll(rid)
+        assert done and info["status"] == qxd.QXD_OK
+    st = eng.stats()
+    assert st["bytes_in_use"] == 0 and st["steps"] > 0
+    eng.close()
+    # same problem through qxd_solve (mixed precision, SAP)
+    x2 = torch.zeros_like(b)
+    rc, info = v.solve(x2, b, tol=1e-10, precond=qxd.QXD_PRECOND_SAP, inner_prec=qxd.QXD_FP32)
+    assert rc == qxd.QXD_OK
+    assert float((x2 - xs[0]).norm() / x2.norm()) < 1e-8
+    for _, vv, _ in reqs:
+        vv.close()
+    for p in parents:
+        p.close()
