@@ -220,6 +220,299 @@ def solve_benchmark(qxd, torch, solvers=("mixed", "fp64_eo", "fp64_full")):
     return out
 
 
+# multi-right-hand-side workload: two lattices, point sources (3 colours x 4
+# spins at a seeded site) for several quarks each, solved together
+BATCH_WORKLOAD = dict(
+    lattices=[dict(T=48, L1=24, L2=24, L3=24, mask=0b1110, seed=3,
+                   quarks=[(m0, q) for m0 in (0.05, 0.1) for q in (-1, 0, 2)]),
+              dict(T=32, L1=16, L2=16, L3=16, mask=0b1110, seed=4, quarks=[(0.05, -1), (0.1, 2)])],
+    eps=0.3, sigma=0.3, csw=1.0, cswqed=1.0, tol=1e-10, budget_gb=120)
+
+# serving workload: Poisson arrivals, sizes (L, T) with probabilities, one
+# resident ensemble per size, m0 ~ U[0.02, 0.2], qhat from {-1, 0, 2}
+SERVE_WORKLOAD = dict(sizes=[(8, 16), (16, 32), (24, 48), (32, 64)], probs=[0.4, 0.3, 0.2, 0.1], n=512,
+                      eps=0.3, sigma=0.3, csw=1.0, cswqed=1.0, m0=(0.02, 0.2), qs=(-1, 0, 2), tol=1e-10,
+                      seed=3000, budget_gb=80, load=0.8)
+
+
+def _fp64_params(qxd):
+    return dict(system=qxd.QXD_SOLVE_EO, inner_prec=qxd.QXD_FP64, max_iter=20000, delta=0.0)
+
+
+def _mixed_params(qxd):
+    return dict(precond=qxd.QXD_PRECOND_SAP, inner_prec=qxd.QXD_FP32)
+
+
+def batch_benchmark(qxd, torch):
+    """All point-source solves of the multi-RHS workload through the engine
+    (one batched launch set per step) against sequential FP64-only solves."""
+    import synth
+    w = BATCH_WORKLOAD
+    lats, ops = [], []
+    for lw in w["lattices"]:
+        su3 = synth.su3_field(lw["T"], lw["L1"], lw["L2"], lw["L3"], w["eps"], synth.SEED_GAUGE + lw["seed"],
+                              device="cuda")
+        ang = synth.u1_field(lw["T"], lw["L1"], lw["L2"], lw["L3"], w["sigma"], synth.SEED_GAUGE + 500 + lw["seed"],
+                             device="cuda")
+        lat = qxd.Lattice(lw["T"], lw["L1"], lw["L2"], lw["L3"], lw["mask"])
+        lat.set_gauge(su3, ang)
+        del su3, ang
+        lats.append(lat)
+        N1 = 2 * lw["L1"]
+        site, src = synth.point_source(lw["T"], N1, lw["L2"], lw["L3"], synth.SEED_SOURCE + lw["seed"])
+        V = lw["T"] * N1 * lw["L2"] * lw["L3"]
+        for m0, q in lw["quarks"]:
+            v = lat.view()
+            v.set_params(m0, w["csw"], w["cswqed"], q)
+            v.sw_build()
+            ops.append((lw, v, m0, q, src.reshape(12, V, 4, 3)))
+    reqs = []  # (op, b)
+    for lw, v, m0, q, src in ops:
+        for k in range(12):
+            reqs.append((v, src[k].cuda()))
+    nreq = len(reqs)
+    # batched D throughput over all right-hand sides (FP32, native layout)
+    handles, ins, outs = [], [], []
+    for v, b in reqs:
+        xn = torch.empty(v.spinor_bytes(qxd.QXD_FP32), dtype=torch.uint8, device="cuda")
+        v.pack(xn, b.to(torch.complex64), qxd.QXD_FP32)
+        handles.append(v.handle)
+        ins.append(xn)
+        outs.append(torch.empty_like(xn))
+    st = torch.cuda.current_stream().cuda_stream
+    args = (handles, [o.data_ptr() for o in outs], [i.data_ptr() for i in ins], qxd.QXD_FP32, 0, st)
+    qxd.qxd_Dw_batch(*args)  # autotunes
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        qxd.qxd_Dw_batch(*args)
+    e1.record()
+    torch.cuda.synchronize()
+    dms = e0.elapsed_time(e1) / 5
+    sites_rhs = sum(v.V for v, _ in reqs)
+    single_bytes = 688 * sites_rhs  # what nreq separate applications would move
+    del ins, outs
+    # engine: every request submitted at once, admitted by budget; the first
+    # pass warms the engine's allocator and the autotuned kernels, the
+    # second is timed
+    eng = qxd.Engine(hbm_budget_bytes=w["budget_gb"] << 30, max_active=nreq)
+    xs = [torch.zeros_like(b) for _, b in reqs]
+    for timed in (False, True):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids = [eng.submit(v, x, b, tol=w["tol"]) for (v, b), x in zip(reqs, xs)]
+        eng.run()
+        t_eng = time.perf_counter() - t0
+        infos = [eng.poll(i)[1] for i in ids]
+        for i in ids:
+            eng.forget(i)
+    stats = eng.stats()
+    eng.close()
+    ok = all(i["status"] == qxd.QXD_OK for i in infos)
+    # sequential references on one request per quark, extrapolated to all
+    seq64, seqmix, diffs = 0.0, 0.0, []
+    for lw, v, m0, q, src in ops:
+        b = src[0].cuda()
+        x64 = torch.zeros_like(b)
+        v.solve(x64, b, tol=w["tol"], **_mixed_params(qxd))  # allocates the view's solver work
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        v.solve(x64, b, tol=w["tol"], **_fp64_params(qxd))
+        seq64 += (time.perf_counter() - t0) * 12
+        xm = torch.zeros_like(b)
+        t0 = time.perf_counter()
+        v.solve(xm, b, tol=w["tol"], **_mixed_params(qxd))
+        seqmix += (time.perf_counter() - t0) * 12
+        k = next(i for i, (vv, bb) in enumerate(reqs) if vv is v)
+        diffs.append(float((xs[k] - x64).norm() / x64.norm()))
+    for _, v, _, _, _ in ops:
+        v.close()
+    for lat in lats:
+        lat.close()
+    return {
+        "workload": "point sources (12 spin-colour) on 48x48x24x24 (L=24, T=48; 2 masses x 3 charges = 72) and "
+                    "32x32x16x16 (L=16, T=32; 24) C* lattices, eps 0.3, tol 1e-10; engine: FGCR + FP32 SAP "
+                    "(4^4, ncy 5, nmr 5) in lockstep, batched launches",
+        "requests": nreq, "all_converged": ok,
+        "max_true_relres": max(i["true_relres"] for i in infos),
+        "engine_s": t_eng, "engine_solves_per_s": nreq / t_eng, "engine_steps": stats["steps"],
+        "sequential_fp64_s_est": seq64, "sequential_fp64_solves_per_s_est": nreq / seq64,
+        "sequential_mixed_s_est": seqmix,
+        "speedup_vs_sequential_fp64": seq64 / t_eng, "speedup_vs_sequential_mixed": seqmix / t_eng,
+        "max_rel_diff_vs_fp64": max(diffs),
+        "note": "sequential times: one solve per quark timed, times 12",
+        "batched_dw": {"rhs": nreq, "ms": dms, "effective_GB_per_s": single_bytes / dms / 1e6,
+                       "note": "688 B per site and right-hand side (the single-RHS byte model) / time"},
+    }
+
+
+def serve_benchmark(qxd, torch):
+    """Continuous batching of a Poisson request stream through the engine."""
+    import numpy as np
+
+    import synth
+    w = SERVE_WORKLOAD
+    rng = np.random.default_rng(w["seed"])
+    n = w["n"]
+    size_idx = rng.choice(len(w["sizes"]), size=n, p=w["probs"])
+    m0s = rng.uniform(*w["m0"], size=n)
+    qs = rng.choice(w["qs"], size=n)
+    ens = []
+    for i, (L, T) in enumerate(w["sizes"]):
+        su3 = synth.su3_field(T, L, L, L, w["eps"], synth.SEED_GAUGE + 10 + i, device="cuda")
+        ang = synth.u1_field(T, L, L, L, w["sigma"], synth.SEED_GAUGE + 510 + i, device="cuda")
+        lat = qxd.Lattice(T, L, L, L, 0b1110)
+        lat.set_gauge(su3, ang)
+        del su3, ang
+        ens.append(lat)
+    pools = [[] for _ in ens]
+    import queue
+    import threading
+    pool_lock = threading.Lock()
+    prep_stream = torch.cuda.Stream()
+
+    def acquire(i, m0, q):
+        with pool_lock:
+            v = pools[i].pop() if pools[i] else None
+        if v is None:
+            v = ens[i].view(stream=prep_stream)
+        v.set_params(float(m0), w["csw"], w["cswqed"], int(q))
+        v.sw_build()
+        return v
+
+    def release(i, v):
+        with pool_lock:
+            pools[i].append(v)
+
+    def source(r):
+        L, T = w["sizes"][size_idx[r]]
+        return synth.spinor_field_device(T, 2 * L, L, L, synth.SEED_SOURCE + 100 + r).reshape(-1, 4, 3)
+
+    # requests in flight per size (each holds a view with its clover term and
+    # its source and solution fields); arrived requests beyond this wait in
+    # a host queue, their latency counted from arrival
+    cap = w.get("inflight_cap", [64, 32, 12, 6])
+    eng = qxd.Engine(hbm_budget_bytes=w["budget_gb"] << 30, max_active=256)
+
+    def run(arrivals):
+        """Serve the requests with arrival times `arrivals` (s). A preparation
+        thread builds each admitted request's operator (view + clover term) and
+        source on its own stream while the main thread steps the engine."""
+        from collections import deque
+        todo, ready = queue.Queue(), queue.Queue()
+
+        def prep():
+            with torch.cuda.stream(prep_stream):
+                while True:
+                    r = todo.get()
+                    if r is None:
+                        return
+                    v = acquire(size_idx[r], m0s[r], qs[r])
+                    b = source(r)
+                    x = torch.zeros_like(b)
+                    prep_stream.synchronize()
+                    ready.put((r, v, x, b))
+
+        worker = threading.Thread(target=prep, daemon=True)
+        worker.start()
+        inflight = {}
+        waiting = [deque() for _ in ens]
+        busy = [0] * len(ens)
+        lat_ms = []
+        nxt = 0
+        done = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while done < n:
+            now = time.perf_counter() - t0
+            while nxt < n and arrivals[nxt] <= now:
+                waiting[size_idx[nxt]].append(nxt)
+                nxt += 1
+            for i in range(len(ens)):
+                while waiting[i] and busy[i] < cap[i]:
+                    todo.put(waiting[i].popleft())
+                    busy[i] += 1
+            while True:
+                try:
+                    r, v, x, b = ready.get_nowait()
+                except queue.Empty:
+                    break
+                rid = eng.submit(v, x, b, tol=w["tol"])
+                inflight[rid] = (r, v, x, b, arrivals[r])
+            a, p, d = eng.step()
+            if d or (a == 0 and p == 0):
+                for rid in list(inflight):
+                    fin, info = eng.poll(rid)
+                    if fin:
+                        r, v, x, b, t_arr = inflight.pop(rid)
+                        if info["status"] != qxd.QXD_OK:
+                            raise RuntimeError(f"request {r} failed: {info}")
+                        lat_ms.append((time.perf_counter() - t0 - t_arr) * 1e3)
+                        release(size_idx[r], v)
+                        busy[size_idx[r]] -= 1
+                        eng.forget(rid)
+                        done += 1
+            if a == 0 and p == 0:
+                if ready.empty() and any(busy):
+                    time.sleep(0.0005)  # the preparation thread is working
+                elif not any(busy) and nxt < n:
+                    time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+        total = time.perf_counter() - t0
+        todo.put(None)
+        worker.join()
+        lat_ms.sort()
+        return total, lat_ms
+
+    # saturated throughput (all requests at t = 0; a first pass warms the
+    # view pools, allocator and autotuned kernels), then Poisson arrivals at
+    # `load` times that rate
+    run(np.zeros(n))
+    t_sat, _ = run(np.zeros(n))
+    rate = w["load"] * n / t_sat
+    arr = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    arr -= arr[0]
+    t_poi, lat_ms = run(arr)
+    eng.close()
+    # one-at-a-time references, one request of each size timed
+    per_size_fp64, per_size_mix = [], []
+    for i in range(len(ens)):
+        r = int(np.nonzero(size_idx == i)[0][0])
+        v = acquire(i, m0s[r], qs[r])
+        b = source(r)
+        v.solve(torch.zeros_like(b), b, tol=w["tol"], **_mixed_params(qxd))  # solver work allocated
+        for kind, store in ((_fp64_params(qxd), per_size_fp64), (_mixed_params(qxd), per_size_mix)):
+            x = torch.zeros_like(b)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            v.set_params(float(m0s[r]), w["csw"], w["cswqed"], int(qs[r]))  # the request's operator
+            v.sw_build()
+            v.solve(x, b, tol=w["tol"], **kind)
+            store.append(time.perf_counter() - t0)
+        release(i, v)
+    counts = np.bincount(size_idx, minlength=len(ens))
+    seq64 = float(np.dot(counts, per_size_fp64))
+    seqmix = float(np.dot(counts, per_size_mix))
+    for pl in pools:
+        for v in pl:
+            v.close()
+    for e in ens:
+        e.close()
+    p50 = lat_ms[len(lat_ms) // 2]
+    p99 = lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))]
+    return {
+        "workload": f"{n} requests, Poisson arrivals, sizes (L,T) {w['sizes']} with p {w['probs']} (C*, doubled), "
+                    "m0 ~ U[0.02,0.2], qhat in {-1,0,2}, Gaussian sources, tol 1e-10",
+        "saturated_solves_per_s": n / t_sat, "arrival_rate_per_s": rate,
+        "poisson_solves_per_s": n / t_poi, "p50_latency_ms": p50, "p99_latency_ms": p99,
+        "one_at_a_time_fp64_solves_per_s_est": n / seq64, "one_at_a_time_mixed_solves_per_s_est": n / seqmix,
+        "speedup_saturated_vs_fp64_one_at_a_time": seq64 / t_sat,
+        "counts_per_size": counts.tolist(),
+        "note": "one-at-a-time rates: one request per size timed (operator build + solve), weighted by the "
+                "size counts",
+    }
+
+
 def sap_benchmark(qxd, torch, steps, w):
     """Time one FP32 SAP application (ncy 5, nmr 5) on the lattice of workload w."""
     su3, ang, psi, V = make_inputs("cuda", w)
@@ -322,7 +615,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="dw", choices=["dw", "solve", "sap"],
+    ap.add_argument("--mode", default="dw", choices=["dw", "solve", "sap", "batch", "serve"],
                     help="dw: the Dw throughput line (plus a solver summary unless --no-solve); "
                          "solve: solver comparison only; sap: time the SAP preconditioner only")
     ap.add_argument("--no-solve", action="store_true")
@@ -343,9 +636,15 @@ def main():
     ge.build()
     from paper_1710_08839_gb300 import qxd
 
-    if args.mode in ("solve", "sap"):
-        res = (solve_benchmark(qxd, torch) if args.mode == "solve"
-               else sap_benchmark(qxd, torch, args.steps, WORKLOADS[args.workload]))
+    if args.mode in ("solve", "sap", "batch", "serve"):
+        if args.mode == "solve":
+            res = solve_benchmark(qxd, torch)
+        elif args.mode == "batch":
+            res = batch_benchmark(qxd, torch)
+        elif args.mode == "serve":
+            res = serve_benchmark(qxd, torch)
+        else:
+            res = sap_benchmark(qxd, torch, args.steps, WORKLOADS[args.workload])
         if rank == 0:
             print(json.dumps({"mode": args.mode, **res}), flush=True)
         return

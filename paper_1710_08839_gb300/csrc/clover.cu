@@ -37,43 +37,6 @@ __device__ __forceinline__ AH3 load_plane(const double* __restrict__ F, size_t V
     return X;
 }
 
-__device__ __forceinline__ void build_block(C64 H[6][6], const AH3& Y1, const AH3& Y2, const AH3& Y3,
-                                            double diag) {
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-            // (1/2) [[ i Y3, i Y1 + Y2 ], [ i Y1 - Y2, -i Y3 ]]
-            H[a][b] = 0.5 * times_i(Y3.a[a][b]);
-            H[a][3 + b] = 0.5 * (times_i(Y1.a[a][b]) + Y2.a[a][b]);
-            H[3 + a][b] = 0.5 * (times_i(Y1.a[a][b]) - Y2.a[a][b]);
-            H[3 + a][3 + b] = 0.5 * times_mi(Y3.a[a][b]);
-        }
-    for (int i = 0; i < 6; ++i) H[i][i] = H[i][i] + mk(diag, 0.0);
-}
-
-__device__ __forceinline__ void store_block(const C64 H[6][6], int blk, double* __restrict__ C64p,
-                                            float4* __restrict__ C32p, size_t V, int s) {
-    float vals[36];
-    for (int i = 0; i < 6; ++i) vals[i] = (float)H[i][i].re;
-    int k = 0;
-    for (int i = 1; i < 6; ++i)
-        for (int j = 0; j < i; ++j, ++k) {
-            vals[6 + 2 * k] = (float)H[i][j].re;
-            vals[6 + 2 * k + 1] = (float)H[i][j].im;
-        }
-    double dv[36];
-    for (int i = 0; i < 6; ++i) dv[i] = H[i][i].re;
-    k = 0;
-    for (int i = 1; i < 6; ++i)
-        for (int j = 0; j < i; ++j, ++k) {
-            dv[6 + 2 * k] = H[i][j].re;
-            dv[6 + 2 * k + 1] = H[i][j].im;
-        }
-    for (int r = 0; r < 36; ++r) C64p[(size_t)(36 * blk + r) * V + s] = dv[r];
-    for (int q = 0; q < 9; ++q)
-        C32p[(size_t)(9 * blk + q) * V + s] =
-            make_float4(vals[4 * q], vals[4 * q + 1], vals[4 * q + 2], vals[4 * q + 3]);
-}
-
 __device__ __forceinline__ double cabs2(C64 a) { return a.re * a.re + a.im * a.im; }
 
 // Gauss-Jordan inverse with partial pivoting; false if singular/non-finite.
@@ -132,37 +95,162 @@ __device__ bool invert6(const C64 H[6][6], C64 B[6][6]) {
     return true;
 }
 
+// LDL^H factorisation of a Hermitian 6x6 block (packed: real diagonal d,
+// strictly lower L row major) and its inverse, all in registers:
+// A = L D L^H, A^-1 = M^H D^-1 M with M = L^-1. Returns false when a pivot
+// falls below 1e-12 of the block norm (the caller then uses Gauss-Jordan
+// with pivoting, which decides singularity).
+__device__ __forceinline__ int lidx6(int i, int j) { return i * (i - 1) / 2 + j; }  // i > j
+
+__device__ __forceinline__ bool ldl_inverse6(const double a_d[6], const C64 a_l[15], double nrm, double i_d[6],
+                                             C64 i_l[15]) {
+    double D[6];
+    C64 L[15];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        double dj = a_d[j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) dj -= cabs2(L[lidx6(j, k)]) * D[k];
+        if (!(fabs(dj) >= 1e-12 * nrm)) return false;
+        D[j] = dj;
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            C64 v = a_l[lidx6(i, j)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) v = v - D[k] * mulc(L[lidx6(i, k)], L[lidx6(j, k)]);
+            L[lidx6(i, j)] = (1.0 / dj) * v;
+        }
+    }
+    // M = L^-1 (unit lower triangular)
+    C64 M[15];
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            C64 v = -L[lidx6(i, j)];
+#pragma unroll
+            for (int k = j + 1; k < i; ++k) v = v - L[lidx6(i, k)] * M[lidx6(k, j)];
+            M[lidx6(i, j)] = v;
+        }
+    // (A^-1)_ij = sum_{k >= i} conj(M_ki) M_kj / D_k for i >= j (M_kk = 1)
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double v = 1.0 / D[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; ++k) v += cabs2(M[lidx6(k, i)]) / D[k];
+        i_d[i] = v;
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            C64 w = (1.0 / D[i]) * M[lidx6(i, j)];
+#pragma unroll
+            for (int k = i + 1; k < 6; ++k) w = w + (1.0 / D[k]) * cmul(M[lidx6(k, i)], M[lidx6(k, j)]);
+            i_l[lidx6(i, j)] = w;
+        }
+    }
+    for (int i = 0; i < 6; ++i)
+        if (!isfinite(i_d[i])) return false;
+    return true;
+}
+
+__device__ __forceinline__ void store_packed(const double d[6], const C64 l[15], int blk, double* __restrict__ C64p,
+                                             float4* __restrict__ C32p, size_t V, int s) {
+    double v[36];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] = d[i];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+        v[6 + 2 * k] = l[k].re;
+        v[7 + 2 * k] = l[k].im;
+    }
+#pragma unroll
+    for (int r = 0; r < 36; ++r) C64p[(size_t)(36 * blk + r) * V + s] = v[r];
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+        C32p[(size_t)(9 * blk + q) * V + s] =
+            make_float4((float)v[4 * q], (float)v[4 * q + 1], (float)v[4 * q + 2], (float)v[4 * q + 3]);
+}
+
+// one thread per (site, block): assemble the block from the field tensors,
+// store it, invert it (LDL^H, Gauss-Jordan with pivoting as the fallback)
 __global__ void __launch_bounds__(128) k_clover_build(Geom g, const double* __restrict__ F, double m0,
                                                       double csw, double u1coef, double* __restrict__ C64p,
                                                       float4* __restrict__ C32p, double* __restrict__ Ci64,
                                                       float4* __restrict__ Ci32, int* __restrict__ bad) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.V) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * g.V) return;
+    const int s = t >> 1, blk = t & 1;
     const size_t V = (size_t)g.V;
+    const double sg = blk == 0 ? 1.0 : -1.0;
     // planes: 0:(0,1) 1:(0,2) 2:(0,3) 3:(1,2) 4:(1,3) 5:(2,3)
-    AH3 X[6];
-    for (int p = 0; p < 6; ++p) X[p] = load_plane(F, V, s, p, csw, u1coef);
-    int nbad = 0;
-    for (int blk = 0; blk < 2; ++blk) {
-        const double sg = blk == 0 ? 1.0 : -1.0;
-        AH3 Y1, Y2, Y3;
+    AH3 Y1, Y2, Y3;
+    {
+        AH3 X0 = load_plane(F, V, s, 0, csw, u1coef), X5 = load_plane(F, V, s, 5, csw, u1coef);
+#pragma unroll
         for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) {
-                Y1.a[a][b] = sg * X[0].a[a][b] - X[5].a[a][b];  // E1 = X23
-                Y2.a[a][b] = sg * X[1].a[a][b] + X[4].a[a][b];  // E2 = X31 = -X13
-                Y3.a[a][b] = sg * X[2].a[a][b] - X[3].a[a][b];  // E3 = X12
-            }
-        C64 H[6][6], Hi[6][6];
-        build_block(H, Y1, Y2, Y3, 4.0 + m0);
-        store_block(H, blk, C64p, C32p, V, s);
-        if (!invert6(H, Hi)) {
-            ++nbad;
-            for (int i = 0; i < 6; ++i)
-                for (int j = 0; j < 6; ++j) Hi[i][j] = mk(0.0, 0.0);
-        }
-        store_block(Hi, blk, Ci64, Ci32, V, s);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) Y1.a[a][b] = sg * X0.a[a][b] - X5.a[a][b];  // E1 = X23
     }
-    if (nbad) atomicAdd(&bad[0], nbad);
+    {
+        AH3 X1 = load_plane(F, V, s, 1, csw, u1coef), X4 = load_plane(F, V, s, 4, csw, u1coef);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) Y2.a[a][b] = sg * X1.a[a][b] + X4.a[a][b];  // E2 = X31 = -X13
+    }
+    {
+        AH3 X2 = load_plane(F, V, s, 2, csw, u1coef), X3 = load_plane(F, V, s, 3, csw, u1coef);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) Y3.a[a][b] = sg * X2.a[a][b] - X3.a[a][b];  // E3 = X12
+    }
+    // packed Hermitian block (1/2) [[ i Y3, i Y1 + Y2 ], [ i Y1 - Y2, -i Y3 ]] + (4 + m0)
+    double d[6];
+    C64 l[15];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const int a = i % 3, sa = i / 3;
+        const C64 yy = sa == 0 ? 0.5 * times_i(Y3.a[a][a]) : 0.5 * times_mi(Y3.a[a][a]);
+        d[i] = 4.0 + m0 + yy.re;
+#pragma unroll
+        for (int j = 0; j < i; ++j) {
+            const int b = j % 3, sb = j / 3;
+            C64 h;
+            if (sa == sb) h = sa == 0 ? 0.5 * times_i(Y3.a[a][b]) : 0.5 * times_mi(Y3.a[a][b]);
+            else h = 0.5 * (times_i(Y1.a[a][b]) - Y2.a[a][b]);  // lower-left block (sa = 1, sb = 0)
+            l[lidx6(i, j)] = h;
+        }
+    }
+    store_packed(d, l, blk, C64p, C32p, V, s);
+    double nrm = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double rs = fabs(d[i]);
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+            if (j != i) rs += sqrt(cabs2(i > j ? l[lidx6(i, j)] : l[lidx6(j, i)]));
+        nrm = fmax(nrm, rs);
+    }
+    double id[6];
+    C64 il[15];
+    bool ok = isfinite(nrm) && nrm > 0.0 && ldl_inverse6(d, l, nrm, id, il);
+    if (!ok) {
+        C64 H[6][6], Hi[6][6];
+        for (int i = 0; i < 6; ++i) {
+            H[i][i] = mk(d[i], 0.0);
+            for (int j = 0; j < i; ++j) {
+                H[i][j] = l[lidx6(i, j)];
+                H[j][i] = conj(l[lidx6(i, j)]);
+            }
+        }
+        ok = invert6(H, Hi);
+        for (int i = 0; i < 6; ++i) {
+            id[i] = ok ? Hi[i][i].re : 0.0;
+            for (int j = 0; j < i; ++j) il[lidx6(i, j)] = ok ? Hi[i][j] : mk(0.0, 0.0);
+        }
+        if (!ok) atomicAdd(&bad[0], 1);
+    }
+    store_packed(id, il, blk, Ci64, Ci32, V, s);
 }
 
 }  // namespace
@@ -172,7 +260,7 @@ int launch_clover_build(qxd_lattice* lat, int* d_bad) {
     QXD_CUDA(cudaMemsetAsync(d_bad, 0, 16, lat->stream));
     // U(1) part of X: cswqed * qhat * (i/4) Im{sum of 4 plaquettes}
     const double u1coef = lat->cswqed * (double)lat->qhat * 0.25;
-    int blocks = (g.V + 127) / 128;
+    int blocks = (2 * g.V + 127) / 128;
     k_clover_build<<<blocks, 128, 0, lat->stream>>>(g, lat->ftens, lat->m0, lat->csw, u1coef, lat->C64,
                                                     lat->C32, lat->Cinv64, lat->Cinv32, d_bad);
     QXD_LAUNCHED("k_clover_build");

@@ -95,9 +95,12 @@ struct Job {
     Clock::time_point t0;
 };
 
+// device bytes a request is expected to hold: four FP64 fields, the FP32
+// residual and up to 6 Krylov pairs (allocated on demand)
 size_t job_bytes(const qxd_lattice* op, int nkv) {
     const size_t V = (size_t)op->g.V;
-    return V * 24 * sizeof(double) * 4 + V * 24 * sizeof(float) * (1 + 2 * (size_t)nkv);
+    const size_t pairs = nkv < 6 ? (size_t)nkv : 6;
+    return V * 24 * sizeof(double) * 4 + V * 24 * sizeof(float) * (1 + 2 * pairs);
 }
 
 }  // namespace
@@ -145,8 +148,8 @@ struct Engine {
         for (void** p : f64)
             if ((rc = pool.alloc(j->f64_bytes, p))) return rc;
         if ((rc = pool.alloc(j->f32_bytes, &j->rin))) return rc;
-        for (int i = 0; i < j->P.nkv; ++i)
-            if ((rc = pool.alloc(j->f32_bytes, &j->phi[i])) || (rc = pool.alloc(j->f32_bytes, &j->chi[i]))) return rc;
+        // Krylov vectors are allocated when first used (SAP-preconditioned
+        // GCR rarely needs all nkv of them)
         return QXD_OK;
     }
 
@@ -247,6 +250,12 @@ struct Engine {
                 }
             if ((rc = blas_batch(red, B_D2F_NATIVE, m, 0, st))) return rc;
         }
+        // Krylov pair k of every job (allocated on first use)
+        for (Job* j : active)
+            if (!j->phi[j->k]) {
+                if ((rc = pool.alloc(j->f32_bytes, &j->phi[j->k])) || (rc = pool.alloc(j->f32_bytes, &j->chi[j->k])))
+                    return rc;
+            }
         // phi_k = P(rin)
         std::vector<SapJob> sj;
         for (Job* j : active) {

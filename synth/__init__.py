@@ -41,6 +41,7 @@ __all__ = [
     "su3_field",
     "u1_field",
     "spinor_field",
+    "spinor_field_device",
     "point_source",
     "extended_extent",
     "SEED_GAUGE",
@@ -143,6 +144,17 @@ def spinor_field(T: int, N1: int, L2: int, L3: int, seed: int,
     z = _normals(2 * n, seed).view(n, 2)
     psi = torch.complex(z[:, 0], z[:, 1]).to(device)
     return psi.view(T, N1, L2, L3, 4, 3)
+
+
+def spinor_field_device(T: int, N1: int, L2: int, L3: int, seed: int, device="cuda") -> torch.Tensor:
+    """Gaussian spinor drawn directly on `device` from a generator of that
+    device seeded with `seed` (a different stream from spinor_field; used when
+    many large sources are needed quickly)."""
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    n = T * N1 * L2 * L3 * 12
+    z = torch.randn(n, 2, dtype=torch.float64, device=device, generator=g)
+    return torch.complex(z[:, 0], z[:, 1]).view(T, N1, L2, L3, 4, 3)
 
 
 def point_source(T: int, N1: int, L2: int, L3: int, seed: int,
