@@ -42,7 +42,7 @@ static int dalloc(T** p, size_t n, const char* what) {
 }
 
 static void free_all(qxd_lattice* L) {
-    void* own[] = {L->C64, L->C32, L->Cinv64, L->Cinv32, L->d_status, L->scratch_in, L->scratch_out,
+    void* own[] = {L->Zq64, L->C64, L->C32, L->Cinv64, L->Cinv32, L->d_status, L->scratch_in, L->scratch_out,
                    L->scratch_lex};
     for (void* p : own)
         if (p) cudaFree(p);
@@ -118,6 +118,7 @@ int qxd_lattice_create(qxd_lattice** out, int T, int L1, int L2, int L3, unsigne
         (rc = dalloc(&lat->Z64, 4 * v, "cudaMalloc(Z64)")) ||
         (rc = dalloc(&lat->A32, v, "cudaMalloc(A32)")) ||
         (rc = dalloc(&lat->ftens, FTENS_REALS * v, "cudaMalloc(ftens)")) ||
+        (rc = dalloc(&lat->Zq64, 4 * v, "cudaMalloc(Zq64)")) ||
         (rc = dalloc(&lat->C64, CLOVER_REALS * v, "cudaMalloc(C64)")) ||
         (rc = dalloc(&lat->C32, CLOVER_F4 * v, "cudaMalloc(C32)")) ||
         (rc = dalloc(&lat->Cinv64, CLOVER_REALS * v, "cudaMalloc(Cinv64)")) ||
@@ -179,7 +180,8 @@ int qxd_lattice_view(qxd_lattice** out, qxd_lattice* parent, void* stream) {
     v->parent = root;
     size_t n = (size_t)root->g.V;
     int rc = 0;
-    if ((rc = dalloc(&v->C64, CLOVER_REALS * n, "cudaMalloc(C64)")) ||
+    if ((rc = dalloc(&v->Zq64, 4 * n, "cudaMalloc(Zq64)")) ||
+        (rc = dalloc(&v->C64, CLOVER_REALS * n, "cudaMalloc(C64)")) ||
         (rc = dalloc(&v->C32, CLOVER_F4 * n, "cudaMalloc(C32)")) ||
         (rc = dalloc(&v->Cinv64, CLOVER_REALS * n, "cudaMalloc(Cinv64)")) ||
         (rc = dalloc(&v->Cinv32, CLOVER_F4 * n, "cudaMalloc(Cinv32)")) ||

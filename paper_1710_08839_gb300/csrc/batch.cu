@@ -84,7 +84,7 @@ Fields<float> op_fields<float>(qxd_lattice* lat) {
 }
 template <>
 Fields<double> op_fields<double>(qxd_lattice* lat) {
-    return Fields<double>{nullptr, nullptr, lat->U64, lat->Z64, lat->C64};
+    return Fields<double>{nullptr, nullptr, lat->U64, lat->Zq64, lat->C64};
 }
 
 // device buffer for group tables, grown on demand, one per (device, stream)

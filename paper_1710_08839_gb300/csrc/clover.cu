@@ -253,6 +253,21 @@ __global__ void __launch_bounds__(128) k_clover_build(Geom g, const double* __re
     store_packed(id, il, blk, Ci64, Ci32, V, s);
 }
 
+// z^qhat per link from z = exp(i A) (binary powering; |z| = 1 so z^-n = conj(z^n))
+__global__ void k_link_phases(int n, const double2* __restrict__ Z, int qhat, double2* __restrict__ Zq) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    C64 b = mk(Z[i].x, Z[i].y), r = mk(1.0, 0.0);
+    int m = qhat < 0 ? -qhat : qhat;
+    while (m) {
+        if (m & 1) r = r * b;
+        b = b * b;
+        m >>= 1;
+    }
+    if (qhat < 0) r = conj(r);
+    Zq[i] = make_double2(r.re, r.im);
+}
+
 }  // namespace
 
 int launch_clover_build(qxd_lattice* lat, int* d_bad) {
@@ -264,6 +279,9 @@ int launch_clover_build(qxd_lattice* lat, int* d_bad) {
     k_clover_build<<<blocks, 128, 0, lat->stream>>>(g, lat->ftens, lat->m0, lat->csw, u1coef, lat->C64,
                                                     lat->C32, lat->Cinv64, lat->Cinv32, d_bad);
     QXD_LAUNCHED("k_clover_build");
+    const int nl = 4 * g.V;
+    k_link_phases<<<(nl + 255) / 256, 256, 0, lat->stream>>>(nl, lat->Z64, lat->qhat, lat->Zq64);
+    QXD_LAUNCHED("k_link_phases");
     return QXD_OK;
 }
 

@@ -84,7 +84,7 @@ int launch_dirac(qxd_lattice* lat, void* out, const void* in, int prec, cudaStre
         if (qnz) k_dirac<float, true><<<blocks, DW_THREADS, 0, st>>>(g, f, (float)lat->qhat);
         else k_dirac<float, false><<<blocks, DW_THREADS, 0, st>>>(g, f, 0.f);
     } else {
-        Fields<double> f{(const double2*)in, (double2*)out, lat->U64, lat->Z64, lat->C64};
+        Fields<double> f{(const double2*)in, (double2*)out, lat->U64, lat->Zq64, lat->C64};
         if (qnz) k_dirac<double, true><<<blocks, DW_THREADS, 0, st>>>(g, f, (double)lat->qhat);
         else k_dirac<double, false><<<blocks, DW_THREADS, 0, st>>>(g, f, 0.0);
     }

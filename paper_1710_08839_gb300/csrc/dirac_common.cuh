@@ -101,8 +101,8 @@ __device__ __forceinline__ void load_link(const double2* __restrict__ U, int V, 
 // [-pi, pi] (|A| <= pi, so only a few periods are removed) and evaluated with
 // the hardware approximation __sincosf, whose absolute error there is ~1e-6,
 // well inside the FP32 tolerance of the operator.
-// FP64: from the stored z = (cos A, sin A), z^qhat by binary powering
-// (|z| = 1, so z^-n = conj(z^n)).
+// FP64: z^qhat stored per operator (built with the clover term from
+// z = (cos A, sin A) by binary powering).
 __device__ __forceinline__ cplx<float> link_phase(const float4* __restrict__ A, int V, int mu, int s, float q) {
     float t = q * reinterpret_cast<const float*>(A + s)[mu];
     const float k = rintf(t * 0.15915494309189535f);
@@ -111,17 +111,9 @@ __device__ __forceinline__ cplx<float> link_phase(const float4* __restrict__ A, 
     __sincosf(t, &sn, &cs);
     return mk(cs, sn);
 }
-__device__ __forceinline__ cplx<double> link_phase(const double2* __restrict__ Z, int V, int mu, int s, double q) {
-    const double2 zz = Z[(size_t)mu * V + s];
-    cplx<double> b = mk(zz.x, zz.y), r = mk(1.0, 0.0);
-    const int qi = (int)q;
-    int n = qi < 0 ? -qi : qi;
-    while (n) {
-        if (n & 1) r = r * b;
-        b = b * b;
-        n >>= 1;
-    }
-    return qi < 0 ? conj(r) : r;
+__device__ __forceinline__ cplx<double> link_phase(const double2* __restrict__ Zq, int V, int mu, int s, double) {
+    const double2 z = Zq[(size_t)mu * V + s];
+    return mk(z.x, z.y);
 }
 
 template <typename R>

@@ -54,7 +54,7 @@ inline Fields<float> fields_of<float>(qxd_lattice* lat) {
 }
 template <>
 inline Fields<double> fields_of<double>(qxd_lattice* lat) {
-    return Fields<double>{nullptr, nullptr, lat->U64, lat->Z64, lat->C64};
+    return Fields<double>{nullptr, nullptr, lat->U64, lat->Zq64, lat->C64};
 }
 template <typename R>
 const typename Fields<R>::cvec* clover_of(qxd_lattice* lat, bool inverse);

@@ -151,7 +151,8 @@ __host__ __device__ __forceinline__ int neighbour_lex(const Geom& g, int x0, int
 // links  FP64 : double2 U[4][9][V]  full 3x3, row major
 // angle  FP32 : float4  A[V]        A(x, mu), mu = 0..3
 // angle  FP64 : double  A[4][V]
-// phase  FP64 : double2 Z[4][V]    z = exp(i A) as (cos A, sin A)
+// phase  FP64 : double2 Z[4][V]    z = exp(i A) as (cos A, sin A); per operator
+//                                   also Zq[4][V] = z^qhat (built with the clover)
 // clover FP32 : float4  C[18][V]    two Hermitian 6x6 blocks (spins {0,1},
 //                                   then {2,3}), 36 floats each: 6 real
 //                                   diagonals, then the 15 complex entries
@@ -235,6 +236,7 @@ struct qxd_lattice {
     double m0 = 0, csw = 0, cswqed = 0;
     int qhat = 0;
     bool has_params = false;
+    double2* Zq64 = nullptr;   // [4][V] z^qhat for this operator's qhat (FP64 kernels)
     double* C64 = nullptr;     // [72][V]
     float4* C32 = nullptr;     // [18][V]
     double* Cinv64 = nullptr;  // [72][V]

@@ -412,7 +412,7 @@ Fields<float> sap_fields<float>(qxd_lattice* lat, void* psi) {
 }
 template <>
 Fields<double> sap_fields<double>(qxd_lattice* lat, void* psi) {
-    return Fields<double>{(const double2*)psi, nullptr, lat->U64, lat->Z64, lat->C64};
+    return Fields<double>{(const double2*)psi, nullptr, lat->U64, lat->Zq64, lat->C64};
 }
 const float4* sap_cinv(qxd_lattice* lat, float) { return lat->Cinv32; }
 const double* sap_cinv(qxd_lattice* lat, double) { return lat->Cinv64; }

@@ -48,6 +48,7 @@ struct SolverWork {
     void* chi[BLAS_KMAX] = {};
     Reducer red;
     SapWork sap;
+    double last_true_rn = 0.0;  // |b - A x| of the last reliable update
     int ensure(int V, int nkv, int prec);
     void release();
 };
