@@ -27,6 +27,10 @@ import subprocess
 import sys
 import time
 
+# the CPU baseline is the plain oracle on one core: keep host BLAS single-threaded
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -147,6 +151,49 @@ def _traffic_record(kernel_files):
         h.update(open(os.path.join(ROOT, f), "rb").read())
     if rec.get("source_sha256") != h.hexdigest():
         return None
+    return rec
+
+
+TRAFFIC_SOURCES = ["paper_1710_08839_gb300/csrc/dirac.cu", "paper_1710_08839_gb300/csrc/dirac_common.cuh"]
+
+
+def write_traffic_record(csv_path):
+    """Per-launch DRAM traffic of the timed kernel from an ncu CSV (metrics
+    gpu__time_duration.sum, dram__bytes_read.sum, dram__bytes_write.sum of
+    k_dirac launches on the full workload) into profiles/, with the hash of
+    the kernel sources it was measured on."""
+    import csv
+    import statistics
+    hdr, per = None, {}
+    for r in csv.reader(open(csv_path)):
+        if r and r[0] == "ID":
+            hdr = r
+            continue
+        if hdr and len(r) == len(hdr):
+            d = dict(zip(hdr, r))
+            if "k_dirac" in d["Kernel Name"]:
+                per.setdefault(d["ID"], {})[d["Metric Name"]] = float(d["Metric Value"])
+    tr = [v["dram__bytes_read.sum"] + v["dram__bytes_write.sum"] for v in per.values()]
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    w = WORKLOAD
+    V = w["T"] * 2 * w["L1"] * w["L2"] * w["L3"]
+    rec = {"kernel": "k_dirac<float, qhat != 0> (FP32 D)", "workload": f"doubled {w['T']}x{2 * w['L1']}x"
+           f"{w['L2']}x{w['L3']} C* lattice, {V} sites", "launches": len(tr),
+           "bytes_per_launch": statistics.mean(tr),
+           "read_bytes_per_launch": statistics.mean(v["dram__bytes_read.sum"] for v in per.values()),
+           "write_bytes_per_launch": statistics.mean(v["dram__bytes_write.sum"] for v in per.values()),
+           "algorithmic_bytes_per_launch": BYTES_PER_SITE_FP32[True] * V,
+           "duration_ns_under_ncu": statistics.mean(v["gpu__time_duration.sum"] for v in per.values()),
+           "command": "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
+                      "--clock-control none -k regex:k_dirac -s 3 -c 5 --csv --log-file dirac_full_dram.csv "
+                      "python bench.py --steps 20 --warmup 3 --no-cpu-baseline --no-solve --no-variants --no-e2e",
+           "source_sha256": h.hexdigest(),
+           "note": "full benchmark size, 1-pass metrics; stale once the kernel sources change"}
+    out = os.path.join(ROOT, "profiles", "dirac_fp32_q2_traffic.json")
+    with open(out, "w") as f:
+        json.dump(rec, f, indent=1)
     return rec
 
 
@@ -619,7 +666,12 @@ def main():
                     help="dw: the Dw throughput line (plus a solver summary unless --no-solve); "
                          "solve: solver comparison only; sap: time the SAP preconditioner only")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--write-traffic", metavar="NCU_CSV",
+                    help="write profiles/dirac_fp32_q2_traffic.json from an ncu CSV of k_dirac launches and exit")
     args = ap.parse_args()
+    if args.write_traffic:
+        print(json.dumps(write_traffic_record(args.write_traffic)))
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -761,8 +813,7 @@ def main():
         torch.cuda.empty_cache()
         solve = solve_benchmark(qxd, torch)
 
-    rec = _traffic_record(["paper_1710_08839_gb300/csrc/dirac.cu",
-                           "paper_1710_08839_gb300/csrc/dirac_common.cuh"])
+    rec = _traffic_record(TRAFFIC_SOURCES)
     traffic = rec["bytes_per_launch"] if rec else None
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
