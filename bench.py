@@ -67,6 +67,25 @@ def _peaks():
     return FALLBACK_HBM, "fallback"
 
 
+def reduce_max(value: float) -> float:
+    """Max of `value` over all ranks (the slowest rank's time); the value
+    itself when no process group is running."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(per_rank_units: float, max_seconds: float, world_size: int) -> float:
+    """Whole-job rate: the units every rank processed (weak scaling: the same
+    per rank) over the slowest rank's time."""
+    return per_rank_units * world_size / max_seconds
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -738,12 +757,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         window["t1"] = time.time()
-        ms = e0.elapsed_time(e1) / steps
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return reduce_max(e0.elapsed_time(e1) / steps)
 
     # headline: FP32, qhat = 2
     xn, yn = native_pair(qxd.QXD_FP32, torch.complex64)
@@ -753,7 +767,7 @@ def main():
     clocks = clk.summary(window["t0"], window["t1"])
     bps = BYTES_PER_SITE_FP32[True]
     gbs_rank = bps * V / (ms * 1e-3) / 1e9
-    value = gbs_rank * ws
+    value = aggregate_value(bps * V / 1e9, ms * 1e-3, ws)
     peak, peak_kind = _peaks()
 
     variants = {}
@@ -787,13 +801,9 @@ def main():
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             lat.Dw(yh, xh)
-        e2e_ms = (time.perf_counter() - t0) / e2e_steps * 1e3
-        if ws > 1:
-            t = torch.tensor([e2e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = reduce_max((time.perf_counter() - t0) / e2e_steps * 1e3)
         _ = float(yh[0, 0, 0].real)  # the step's result is on the host
-        e2e = {"value": bps * V / (e2e_ms * 1e-3) / 1e9 * ws, "unit": "GB/s",
+        e2e = {"value": aggregate_value(bps * V / 1e9, e2e_ms * 1e-3, ws), "unit": "GB/s",
                "h2d_bytes_per_step": V * 96, "d2h_bytes_per_step": V * 96, "ms_per_step": e2e_ms}
         del xh, yh
 

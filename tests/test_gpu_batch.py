@@ -191,3 +191,52 @@ def test_engine_admission_by_budget_and_agreement_with_solve():
         vv.close()
     for p in parents:
         p.close()
+
+
+def test_engine_not_converged_and_argument_errors():
+    from paper_1710_08839_gb300 import qxd
+    c = Case(T=8, L1=8, L2=8, L3=8, qhat=2, m0=0.05)
+    lat = c.lattice()
+    b = c.psi.cuda()
+    eng = qxd.Engine(hbm_budget_bytes=8 << 30, max_active=4)
+    x = torch.zeros_like(b)
+    rid = eng.submit(lat, x, b, tol=1e-14, max_iter=2)
+    eng.run()
+    done, info = eng.poll(rid)
+    assert done and info["status"] == qxd.QXD_ERR_NOT_CONVERGED
+    assert info["iterations"] == 2 and 0 < info["true_relres"] < 1
+    assert torch.count_nonzero(x) > 0
+    for kw in ({"system": qxd.QXD_SOLVE_EO}, {"inner_prec": qxd.QXD_FP64}, {"nkv": 17}, {"tol": 0.0}):
+        with pytest.raises(qxd.QxdError) as e:
+            eng.submit(lat, torch.zeros_like(b), b, **kw)
+        assert e.value.code == qxd.QXD_ERR_ARG
+    fresh = lat.view()                     # parameters never set: no clover term
+    with pytest.raises(qxd.QxdError) as e:
+        eng.submit(fresh, torch.zeros_like(b), b)
+    assert e.value.code == qxd.QXD_ERR_STATE
+    with pytest.raises(qxd.QxdError):
+        eng.forget(123456)
+    eng.close()
+    fresh.close()
+    lat.close()
+
+
+def test_native_layout_solve_matches_lexicographic():
+    from paper_1710_08839_gb300 import qxd
+    c = Case(T=8, L1=8, L2=8, L3=8, qhat=-1, m0=0.1)
+    lat = c.lattice()
+    b = c.psi.cuda()
+    x_lex = torch.zeros_like(b)
+    rc, _ = lat.solve(x_lex, b, tol=1e-10, precond=qxd.QXD_PRECOND_SAP, inner_prec=qxd.QXD_FP32)
+    assert rc == qxd.QXD_OK
+    bn = torch.empty(lat.spinor_bytes(qxd.QXD_FP64), dtype=torch.uint8, device="cuda")
+    lat.pack(bn, b, qxd.QXD_FP64)
+    xn = torch.zeros_like(bn)
+    rc, _ = lat.solve(xn, bn, tol=1e-10, precond=qxd.QXD_PRECOND_SAP, inner_prec=qxd.QXD_FP32,
+                      flags=qxd.QXD_LAYOUT_NATIVE)
+    assert rc == qxd.QXD_OK
+    x2 = torch.empty_like(b)
+    lat.unpack(x2, xn, qxd.QXD_FP64)
+    torch.cuda.synchronize()
+    assert torch.equal(x2, x_lex)
+    lat.close()
