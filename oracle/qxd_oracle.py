@@ -260,6 +260,10 @@ def _as_field_fn(psi):
     return lambda idx: psi[..., idx, :, :]
 
 
+# lattices up to this many sites keep the SW matrices of all sites
+_SW_CACHE_SITES = 1 << 16
+
+
 class Dirac:
     """D = m0 + Dw + dDsw for one quark of integer charge qhat (Eq. (16)-(23)).
 
@@ -360,9 +364,13 @@ class Dirac:
 
         The matrices of the whole lattice are computed once and kept."""
         idx = np.asarray(idx, dtype=np.int64)
+        cached = getattr(self, "_sw_all", None)
+        if cached is None and self.lat.V <= _SW_CACHE_SITES:
+            # small lattice: build every site's matrix once, index it after
+            cached = self._sw_all = self._sw_matrix(self.lat.all_sites())
+        if cached is not None:
+            return cached[idx]
         full = idx.shape == (self.lat.V,) and idx[0] == 0 and idx[-1] == self.lat.V - 1
-        if full and getattr(self, "_sw_all", None) is not None:
-            return self._sw_all
         out = self._sw_matrix(idx)
         if full and np.array_equal(idx, self.lat.all_sites()):
             self._sw_all = out
