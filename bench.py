@@ -579,6 +579,96 @@ def serve_benchmark(qxd, torch):
     }
 
 
+# pseudofermion action: the factor P_1 of the paper's rational approximation
+# (Table 2, seven zero/pole pairs, solved by multi-shift CG) on the solver
+# workload's lattice
+RATIONAL_WORKLOAD = dict(points=[(0.05, -1), (0.05, 2)], factor=1, tol=1e-10, reps=2)
+
+
+def table2_factor(k):
+    """(nu, mu) of factor P_k from the Table 2 fixture (zeros, poles, factor)."""
+    nu, mu = [], []
+    with open(os.path.join(ROOT, "tests", "golden", "table2_rational.txt")) as f:
+        for ln in f:
+            if ln.strip() and not ln.startswith("#"):
+                _, n_j, m_j, fac = ln.split()
+                if int(fac) == k:
+                    nu.append(float(n_j))
+                    mu.append(float(m_j))
+    return nu, mu
+
+
+# algorithmic bytes per even site of one multi-shift CG step (FP64): two
+# applications of Q = gamma5 D_hat, each an M_oo^-1 H_oe kernel (spinor in and
+# out 192 + 192, the 8 links of the site 8 x 144, their U(1) factors 8 x 16,
+# clover inverse 576) and a M_ee - H_eo kernel (the same plus the aux spinor
+# 192); |Q p|^2 (192); r -= alpha (w + s p) (4 x 192); and per active shift
+# x += a p, p = z r + b p (4 x 192, plus r once)
+MSCG_BYTES_Q = (192 + 192 + 8 * 144 + 8 * 16 + 576) + (3 * 192 + 8 * 144 + 8 * 16 + 576)
+MSCG_BYTES_FIXED = 2 * MSCG_BYTES_Q + 192 + 4 * 192 + 192
+MSCG_BYTES_PER_SHIFT = 4 * 192
+
+
+def rational_benchmark(qxd, torch):
+    """P_1 phi by one multi-shift CG over its seven poles, against the same
+    seven systems solved one at a time; wall time of the synchronous calls."""
+    w = SOLVE_WORKLOAD
+    R = RATIONAL_WORKLOAD
+    su3, ang, psi, V = make_inputs("cuda", w)
+    phi = psi.cuda()
+    del psi
+    lat = qxd.Lattice(w["T"], w["L1"], w["L2"], w["L3"], w["mask"])
+    lat.set_gauge(su3, ang)
+    del su3, ang
+    nu, mu = table2_factor(R["factor"])
+    out = torch.empty_like(phi)
+    x1 = [torch.empty_like(phi)]
+    Vh = V // 2
+    rows = []
+    t_multi = t_single = 0.0
+    for m0, q in R["points"]:
+        lat.set_params(m0, w["csw"], w["cswqed"], q)
+        lat.sw_build()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        logdet = lat.sw_logdet(qxd.QXD_SITES_ODD)
+        t_ld = time.perf_counter() - t0
+        lat.rational_apply(out, phi, nu, mu, tol=R["tol"])  # allocates the work vectors
+        ms = []
+        for _ in range(R["reps"]):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, info = lat.rational_apply(out, phi, nu, mu, tol=R["tol"])
+            ms.append((time.perf_counter() - t0) * 1e3)
+        t_multi += min(ms) / 1e3
+        it = info["iterations"]
+        # the seven systems one at a time (plain CG each)
+        single = []
+        for m_j in mu:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc1, info1, rel1 = lat.mscg(x1, phi, [m_j * m_j], tol=R["tol"])
+            single.append({"ms": (time.perf_counter() - t0) * 1e3, "iterations": info1["iterations"],
+                           "status": rc1})
+        t_single += sum(s["ms"] for s in single) / 1e3
+        # bytes of the CG steps: every shift is active until it converges;
+        # counted here as if all stayed active (an upper bound on the work)
+        bytes_it = Vh * (MSCG_BYTES_FIXED + len(mu) * MSCG_BYTES_PER_SHIFT)
+        rows.append({"m0": m0, "qhat": q, "status": rc, "ms": min(ms), "iterations": it,
+                     "ms_per_iteration": min(ms) / max(it, 1), "true_relres": info["true_relres"],
+                     "action": info["action"], "ln_abs_det_Doo": logdet, "logdet_ms": t_ld * 1e3,
+                     "GBs_per_iteration_model": bytes_it / (min(ms) / 1e3 / max(it, 1)) / 1e9,
+                     "single_shift_cg": single})
+    lat.close()
+    n = len(R["points"])
+    return {"workload": "P_1 of Table 2 (7 zero/pole pairs) by FP64 multi-shift CG on D_hat^dag D_hat, "
+                        "doubled 64x64x32x32 C* lattice (L=32, T=64), eps 0.3, csw=cswqed=1, tol 1e-10 "
+                        "per shift (true FP64 residual)",
+            "points": rows, "rational_applies_per_s": n / t_multi,
+            "speedup_multishift_vs_7_single_cg": t_single / t_multi,
+            "bytes_per_even_site_per_iteration": MSCG_BYTES_FIXED + len(mu) * MSCG_BYTES_PER_SHIFT}
+
+
 def sap_benchmark(qxd, torch, steps, w):
     """Time one FP32 SAP application (ncy 5, nmr 5) on the lattice of workload w."""
     su3, ang, psi, V = make_inputs("cuda", w)
@@ -689,9 +779,10 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="dw", choices=["dw", "solve", "sap", "batch", "serve"],
+    ap.add_argument("--mode", default="dw", choices=["dw", "solve", "sap", "batch", "serve", "rational"],
                     help="dw: the Dw throughput line (plus a solver summary unless --no-solve); "
-                         "solve: solver comparison only; sap: time the SAP preconditioner only")
+                         "solve: solver comparison only; sap: time the SAP preconditioner only; "
+                         "batch / serve: multi-RHS and serving workloads; rational: pseudofermion action")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--write-traffic", metavar="NCU_CSV",
                     help="write profiles/dirac_fp32_q2_traffic.json from an ncu CSV of k_dirac launches and exit")
@@ -715,9 +806,11 @@ def main():
     ge.build()
     from paper_1710_08839_gb300 import qxd
 
-    if args.mode in ("solve", "sap", "batch", "serve"):
+    if args.mode in ("solve", "sap", "batch", "serve", "rational"):
         if args.mode == "solve":
             res = solve_benchmark(qxd, torch)
+        elif args.mode == "rational":
+            res = rational_benchmark(qxd, torch)
         elif args.mode == "batch":
             res = batch_benchmark(qxd, torch)
         elif args.mode == "serve":

@@ -311,6 +311,80 @@ int qxd_engine_run(qxd_engine* e);
 /* device bytes of active requests, bytes held by the allocator, steps so far */
 int qxd_engine_stats(const qxd_engine* e, size_t* bytes_in_use, size_t* bytes_held, long long* steps);
 
+/* ---------------------------------------------------------------------------
+ * Pseudofermion action of the RHMC (Sec. 2.4):
+ *   S_pf = -1/2 ln|Det D_oo| + sum_k phi_k^dag P_k phi_k,
+ *   P_k  = prod_j (D_hat^dag D_hat + nu_j^2) / (D_hat^dag D_hat + mu_j^2),
+ * with D_hat = D_ee - D_eo D_oo^-1 D_oe the even-odd operator and phi_k
+ * fields on the even sites. D_hat^dag = gamma5 D_hat gamma5 (gamma5
+ * hermiticity of D). All of this is FP64.
+ * ------------------------------------------------------------------------- */
+#define QXD_SITES_EVEN 0
+#define QXD_SITES_ODD 1
+#define QXD_SITES_ALL 2
+
+/*
+ * *out = sum over the sites x of the selected parity of ln|det M(x)|, with
+ * M(x) the 12x12 site-diagonal block of D (4 + m0 plus the SW term, the two
+ * 6x6 chirality blocks of qxd_sw_build). sites = QXD_SITES_ODD gives
+ * ln|Det D_oo|, the exact term of S_pf (Sec. 2.4: D_oo is diagonal in the
+ * lattice index, so its determinant is computed exactly). Each block's
+ * determinant is taken by Gaussian elimination with partial pivoting; the
+ * sum is reduced in a fixed order (same result on every call). Returns
+ * QXD_ERR_SW_SINGULAR if a block is exactly singular or the result is not
+ * finite, QXD_ERR_STATE before qxd_sw_build. Synchronises the lattice's stream.
+ */
+int qxd_sw_logdet(qxd_lattice* lat, int sites, double* out);
+
+typedef struct {
+    double tol;       /* stop when each shift's residual is <= tol |b|             */
+    int max_iter;     /* limit on CG steps                                        */
+    int flags;        /* x and b: QXD_DEVICE | QXD_HOST, QXD_LAYOUT_LEX | _NATIVE  */
+} qxd_mscg_params;
+
+typedef struct {
+    int status;             /* QXD_OK, QXD_ERR_NOT_CONVERGED, QXD_ERR_NUMERIC       */
+    int iterations;         /* CG steps                                             */
+    double true_relres;     /* max over shifts of |b - (A + s_j) x_j| / |b| (FP64)   */
+    double action;          /* qxd_rational_apply: Re <phi, P phi>; else 0           */
+    double time_ms;         /* wall time of the call                                */
+    int dhat_calls;         /* applications of D_hat (A costs two)                  */
+} qxd_mscg_info;
+
+/* Defaults: tol 1e-10, max_iter 10000, device lexicographic buffers. */
+void qxd_mscg_defaults(qxd_mscg_params* p);
+
+/*
+ * Multi-shift CG: x[j] = (D_hat^dag D_hat + sigma[j])^-1 b for j < nshift
+ * (1 <= nshift <= 16, sigma[j] >= 0, any order), all from one Krylov space
+ * (the paper solves its rational factors with multi-shift CG, Sec. 2.4 and
+ * App. A, without giving the method; this is the standard shifted CG, whose
+ * residuals of all shifts stay collinear with the base residual).
+ * b and x[j]: full-lattice FP64 spinor fields (layout and location by
+ * params->flags); only the even sites of b are read, the odd sites of each
+ * x[j] are set to zero. The smallest shift is the base system; a shift stops
+ * updating once its residual is below tol |b|. At the end each shift's
+ * true residual is recomputed in FP64 (relres[j] if relres is not NULL;
+ * the largest in info->true_relres). Returns QXD_ERR_NOT_CONVERGED (x and
+ * info still written) when a true residual exceeds tol. Work vectors are
+ * allocated on the first call and kept with the lattice. Synchronises.
+ */
+int qxd_mscg(qxd_lattice* lat, int nshift, const double* sigma, void* const* x, const void* b,
+             const qxd_mscg_params* params, qxd_mscg_info* info, double* relres, void* stream);
+
+/*
+ * out = P phi with P = prod_{j<n} (A + nu[j]^2) / (A + mu[j]^2),
+ * A = D_hat^dag D_hat (one frequency-splitting factor P_k of Sec. 2.4, or a
+ * Hasenbusch ratio), computed as phi + sum_j rho_j (A + mu[j]^2)^-1 phi with
+ * the partial-fraction residues rho_j = prod_l (nu_l^2 - mu_j^2) /
+ * prod_{l != j} (mu_l^2 - mu_j^2) and one qxd_mscg over the shifts mu[j]^2.
+ * info->action = Re <phi, P phi> (the factor's term of S_pf). The mu[j]
+ * must be distinct and 1 <= n <= 16. Fields and flags as qxd_mscg (odd sites
+ * of out set to zero). The tolerance applies to each shifted solve.
+ */
+int qxd_rational_apply(qxd_lattice* lat, int n, const double* nu, const double* mu, void* out, const void* phi,
+                       const qxd_mscg_params* params, qxd_mscg_info* info, void* stream);
+
 /* Bytes of one spinor field in the native layout for precision `prec`. */
 size_t qxd_spinor_bytes(const qxd_lattice* lat, int prec);
 

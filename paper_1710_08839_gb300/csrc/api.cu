@@ -140,6 +140,7 @@ int qxd_lattice_destroy(qxd_lattice* lat) {
     cudaStreamSynchronize(lat->stream);
     if (lat->parent) --lat->parent->nviews;
     release_solver(lat);
+    release_mscg(lat);
     free_all(lat);
     delete lat;
     return QXD_OK;

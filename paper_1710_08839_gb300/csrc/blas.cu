@@ -15,27 +15,6 @@ __device__ __forceinline__ double2 ld(const double2* p, size_t i) { return p[i];
 __device__ __forceinline__ void st_(float2* p, size_t i, double2 v) { p[i] = make_float2((float)v.x, (float)v.y); }
 __device__ __forceinline__ void st_(double2* p, size_t i, double2 v) { p[i] = v; }
 
-// block-wide sum of NC values per thread into partials[blockIdx.x][0..NC)
-template <int NC>
-__device__ __forceinline__ void block_reduce_store(double v[NC], int nc, double* __restrict__ partials) {
-    __shared__ double sh[RED_THREADS / 32][2 * BLAS_KMAX];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        if (c >= nc) break;
-        double x = v[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) sh[warp][c] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x < nc) {
-        double x = 0.0;
-        for (int w = 0; w < RED_THREADS / 32; ++w) x += sh[w][threadIdx.x];
-        partials[(size_t)blockIdx.x * 2 * BLAS_KMAX + threadIdx.x] = x;
-    }
-}
-
 __global__ void k_reduce_final(const double* __restrict__ partials, int nc, double* __restrict__ res) {
     const int c = threadIdx.x;
     if (c >= nc) return;
@@ -183,20 +162,20 @@ __global__ void k_f2d(size_t n, const float2* __restrict__ in, double2* __restri
         out[i] = make_double2(in[i].x, in[i].y);
 }
 
-int finish(Reducer& red, int nc, cudaStream_t st) {
-    k_reduce_final<<<1, 2 * BLAS_KMAX, 0, st>>>(red.partials, nc, red.d_res);
-    QXD_LAUNCHED("k_reduce_final");
-    QXD_CUDA(cudaMemcpyAsync(red.h_res, red.d_res, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
-    QXD_CUDA(cudaStreamSynchronize(st));
-    return QXD_OK;
-}
-
 inline int ew_blocks(size_t n) {
     size_t b = (n + 255) / 256;
     return (int)(b < 4 * 152 * 4 ? b : 4 * 152 * 4);
 }
 
 }  // namespace
+
+int reduce_finish(Reducer& red, int nc, cudaStream_t st) {
+    k_reduce_final<<<1, 2 * BLAS_KMAX, 0, st>>>(red.partials, nc, red.d_res);
+    QXD_LAUNCHED("k_reduce_final");
+    QXD_CUDA(cudaMemcpyAsync(red.h_res, red.d_res, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QXD_CUDA(cudaStreamSynchronize(st));
+    return QXD_OK;
+}
 
 int Reducer::init() {
     if (partials) return QXD_OK;
@@ -218,7 +197,7 @@ int blas_mdot(Reducer& red, size_t n, int k, const VecList<T>& xs, const T* y, c
     if (k <= 0) return QXD_OK;
     k_mdot<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, xs, y, red.partials);
     QXD_LAUNCHED("k_mdot");
-    int rc = finish(red, 2 * k, st);
+    int rc = reduce_finish(red, 2 * k, st);
     if (rc) return rc;
     for (int j = 0; j < k; ++j) out[j] = cd(red.h_res[2 * j], red.h_res[2 * j + 1]);
     return QXD_OK;
@@ -228,7 +207,7 @@ template <typename T>
 int blas_norm2(Reducer& red, size_t n, const T* x, double* out, cudaStream_t st) {
     k_norm2<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, x, red.partials);
     QXD_LAUNCHED("k_norm2");
-    int rc = finish(red, 1, st);
+    int rc = reduce_finish(red, 1, st);
     if (rc) return rc;
     *out = red.h_res[0];
     return QXD_OK;
@@ -239,7 +218,7 @@ int blas_maxpy_norm(Reducer& red, size_t n, int k, const CoefList& c, const VecL
                     cudaStream_t st) {
     k_maxpy_norm<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, c, xs, y, red.partials);
     QXD_LAUNCHED("k_maxpy_norm");
-    int rc = finish(red, 1, st);
+    int rc = reduce_finish(red, 1, st);
     if (rc) return rc;
     *nrm2 = red.h_res[0];
     return QXD_OK;
@@ -285,7 +264,7 @@ int blas_sub_norm(Reducer& red, size_t n, const double2* b, const double2* t, do
                   cudaStream_t st) {
     k_sub_norm<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, b, t, r, red.partials);
     QXD_LAUNCHED("k_sub_norm");
-    int rc = finish(red, 1, st);
+    int rc = reduce_finish(red, 1, st);
     if (rc) return rc;
     *nrm2 = red.h_res[0];
     return QXD_OK;

@@ -35,6 +35,31 @@ struct Reducer {
 
 using cd = std::complex<double>;
 
+// block-wide sum of NC values per thread into partials[blockIdx.x][0..NC)
+template <int NC>
+__device__ __forceinline__ void block_reduce_store(const double v[NC], int nc, double* __restrict__ partials) {
+    __shared__ double sh[RED_THREADS / 32][2 * BLAS_KMAX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        if (c >= nc) break;
+        double x = v[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[warp][c] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < nc) {
+        double x = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) x += sh[w][threadIdx.x];
+        partials[(size_t)blockIdx.x * 2 * BLAS_KMAX + threadIdx.x] = x;
+    }
+}
+
+// sums the RED_BLOCKS partials of the first nc values in a fixed order into
+// red.h_res[0..nc) (synchronises the stream)
+int reduce_finish(Reducer& red, int nc, cudaStream_t st);
+
 // out[j] = <x_j, y> = sum conj(x_j) y, j < k   (synchronises the stream)
 template <typename T>
 int blas_mdot(Reducer& red, size_t n, int k, const VecList<T>& xs, const T* y, cd* out, cudaStream_t st);

@@ -9,6 +9,7 @@
 //   CLOVER_AUX_MHOP  out = M aux - H psi
 //   AUX_MHOP         out = aux - H psi
 //   INV_AUX_MHOP     out = M^-1 (aux - H psi)
+//   G5_CLOVER_AUX_MHOP  out = gamma5 (M aux - H psi)
 // where psi lives on the other parity. Each field is addressed as
 // (pointer, stride, offset): element k of the site with native index s is at
 // p[k * stride + s - offset], so full-lattice arrays (stride V, offset 0)
@@ -48,12 +49,17 @@ __global__ void __launch_bounds__(DW_THREADS, DwMinBlocksEo<R>::value)
 #pragma unroll
         for (int i = 0; i < 12; ++i) t[i] = R(-0.5) * acc[i];
         clover_mul(Cl, g.V, s, t, w);
-    } else if (MODE == EO_CLOVER_AUX_MHOP) {
+    } else if (MODE == EO_CLOVER_AUX_MHOP || MODE == EO_G5_CLOVER_AUX_MHOP) {
         cplx<R> a[12];
         load_spinor(aux.p, aux.stride, s - aux.off, a);
         clover_mul(Cl, g.V, s, a, w);
 #pragma unroll
         for (int i = 0; i < 12; ++i) w[i] = w[i] + R(0.5) * acc[i];
+        if (MODE == EO_G5_CLOVER_AUX_MHOP) {
+            // gamma5 = diag(1, 1, -1, -1): spins 2 and 3 change sign
+#pragma unroll
+            for (int i = 6; i < 12; ++i) w[i] = R(-1) * w[i];
+        }
     } else if (MODE == EO_AUX_MHOP) {
         load_spinor(aux.p, aux.stride, s - aux.off, w);
 #pragma unroll
@@ -92,6 +98,7 @@ int launch_mode(qxd_lattice* lat, int mode, int p, const Fields<R>& f, SpRef<R> 
         case EO_INV_HOP: k_dslash_half<R, QNZ, EO_INV_HOP><<<blocks, DW_THREADS, 0, st>>>(g, p, f, in, aux, out, Cl, q); break;
         case EO_CLOVER_AUX_MHOP: k_dslash_half<R, QNZ, EO_CLOVER_AUX_MHOP><<<blocks, DW_THREADS, 0, st>>>(g, p, f, in, aux, out, Cl, q); break;
         case EO_AUX_MHOP: k_dslash_half<R, QNZ, EO_AUX_MHOP><<<blocks, DW_THREADS, 0, st>>>(g, p, f, in, aux, out, Cl, q); break;
+        case EO_G5_CLOVER_AUX_MHOP: k_dslash_half<R, QNZ, EO_G5_CLOVER_AUX_MHOP><<<blocks, DW_THREADS, 0, st>>>(g, p, f, in, aux, out, Cl, q); break;
         default: k_dslash_half<R, QNZ, EO_INV_AUX_MHOP><<<blocks, DW_THREADS, 0, st>>>(g, p, f, in, aux, out, Cl, q); break;
     }
     QXD_LAUNCHED("k_dslash_half");
@@ -132,6 +139,14 @@ int apply_dhat(qxd_lattice* lat, SpRefOut<R> out_e, SpRef<R> in_e, SpRefOut<R> t
 }
 template int apply_dhat<float>(qxd_lattice*, SpRefOut<float>, SpRef<float>, SpRefOut<float>, cudaStream_t);
 template int apply_dhat<double>(qxd_lattice*, SpRefOut<double>, SpRef<double>, SpRefOut<double>, cudaStream_t);
+
+template <typename R>
+int apply_g5dhat(qxd_lattice* lat, SpRefOut<R> out_e, SpRef<R> in_e, SpRefOut<R> tmp_o, cudaStream_t st) {
+    int rc = launch_eo<R>(lat, EO_INV_HOP, 1, in_e, SpRef<R>{}, tmp_o, true, st);
+    if (rc) return rc;
+    return launch_eo<R>(lat, EO_G5_CLOVER_AUX_MHOP, 0, as_in(tmp_o), in_e, out_e, false, st);
+}
+template int apply_g5dhat<double>(qxd_lattice*, SpRefOut<double>, SpRef<double>, SpRefOut<double>, cudaStream_t);
 
 namespace {
 

@@ -5,7 +5,8 @@
 
 namespace qxd {
 
-enum { EO_HOP = 0, EO_INV_HOP = 1, EO_CLOVER_AUX_MHOP = 2, EO_AUX_MHOP = 3, EO_INV_AUX_MHOP = 4 };
+enum { EO_HOP = 0, EO_INV_HOP = 1, EO_CLOVER_AUX_MHOP = 2, EO_AUX_MHOP = 3, EO_INV_AUX_MHOP = 4,
+       EO_G5_CLOVER_AUX_MHOP = 5 };
 
 template <typename R>
 using DwMinBlocksEo = DwMinBlocks<R>;
@@ -74,5 +75,8 @@ template <typename R>
 int launch_clover_half(qxd_lattice* lat, int p, SpRef<R> in, SpRefOut<R> out, bool inverse, cudaStream_t st);
 template <typename R>
 int apply_dhat(qxd_lattice* lat, SpRefOut<R> out_e, SpRef<R> in_e, SpRefOut<R> tmp_o, cudaStream_t st);
+// gamma5 D_hat psi_e (Hermitian: D_hat^dag = gamma5 D_hat gamma5)
+template <typename R>
+int apply_g5dhat(qxd_lattice* lat, SpRefOut<R> out_e, SpRef<R> in_e, SpRefOut<R> tmp_o, cudaStream_t st);
 
 }  // namespace qxd

@@ -214,6 +214,7 @@ __host__ __device__ __forceinline__ cplx<R> times_mi(cplx<R> a) { return {a.im, 
 // the lattice object
 // ---------------------------------------------------------------------------
 struct SolverWork;
+struct MscgWork;
 }  // namespace qxd
 
 struct qxd_lattice {
@@ -250,6 +251,7 @@ struct qxd_lattice {
     void* scratch_lex = nullptr;  // lexicographic FP64 spinor
 
     qxd::SolverWork* solver = nullptr;  // Krylov work vectors (first solve)
+    qxd::MscgWork* mscg = nullptr;      // multi-shift CG work vectors (first use)
 
     // views: a view shares the gauge field of its parent and owns its own
     // parameters, clover term, scratch and solver work
@@ -277,4 +279,5 @@ inline bool clover_ready(const qxd_lattice* lat) {
     return lat->has_clover && lat->built_gauge_version == gauge_owner(lat)->gauge_version;
 }
 void release_solver(qxd_lattice* lat);
+void release_mscg(qxd_lattice* lat);
 }  // namespace qxd

@@ -40,6 +40,10 @@ QXD_PRECOND_SAP = 1
 QXD_SOLVE_FULL = 0
 QXD_SOLVE_EO = 1
 
+QXD_SITES_EVEN = 0
+QXD_SITES_ODD = 1
+QXD_SITES_ALL = 2
+
 _STATUS_NAMES = {
     0: "QXD_OK", -1: "QXD_ERR_ARG", -2: "QXD_ERR_OOM", -3: "QXD_ERR_CUDA",
     -4: "QXD_ERR_NOT_ADMISSIBLE", -5: "QXD_ERR_SW_SINGULAR", -6: "QXD_ERR_NOT_CONVERGED",
@@ -71,6 +75,19 @@ class qxd_solve_info(ctypes.Structure):
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
+
+class qxd_mscg_params(ctypes.Structure):
+    _fields_ = [("tol", _d), ("max_iter", _i), ("flags", _i)]
+
+
+class qxd_mscg_info(ctypes.Structure):
+    _fields_ = [("status", _i), ("iterations", _i), ("true_relres", _d), ("action", _d),
+                ("time_ms", _d), ("dhat_calls", _i)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # name -> (restype, argtypes); mirrors include/qxd.h
 SIGNATURES = {
     "qxd_lattice_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, ctypes.c_uint, _vp]),
@@ -99,6 +116,12 @@ SIGNATURES = {
     "qxd_engine_run": (_i, [_vp]),
     "qxd_engine_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
                               ctypes.POINTER(ctypes.c_longlong)]),
+    "qxd_sw_logdet": (_i, [_vp, _i, ctypes.POINTER(_d)]),
+    "qxd_mscg_defaults": (None, [ctypes.POINTER(qxd_mscg_params)]),
+    "qxd_mscg": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_vp), _vp, ctypes.POINTER(qxd_mscg_params),
+                      ctypes.POINTER(qxd_mscg_info), ctypes.POINTER(_d), _vp]),
+    "qxd_rational_apply": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp, _vp,
+                                ctypes.POINTER(qxd_mscg_params), ctypes.POINTER(qxd_mscg_info), _vp]),
     "qxd_spinor_bytes": (ctypes.c_size_t, [_vp, _i]),
     "qxd_spinor_pack": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_spinor_unpack": (_i, [_vp, _vp, _vp, _i, _vp]),
@@ -198,6 +221,44 @@ def qxd_solve(lat, x_ptr, b_ptr, params: qxd_solver_params, stream=0):
     """Returns (status, info); status QXD_ERR_NOT_CONVERGED does not raise."""
     info = qxd_solve_info()
     rc = _call("qxd_solve", lat, x_ptr, b_ptr, ctypes.byref(params), ctypes.byref(info), stream)
+    if rc not in (QXD_OK, QXD_ERR_NOT_CONVERGED):
+        check(rc)
+    return rc, info
+
+
+def qxd_sw_logdet(lat, sites) -> float:
+    out = _d()
+    check(_call("qxd_sw_logdet", lat, sites, ctypes.byref(out)))
+    return out.value
+
+
+def qxd_mscg_defaults() -> qxd_mscg_params:
+    p = qxd_mscg_params()
+    _call("qxd_mscg_defaults", ctypes.byref(p))
+    return p
+
+
+def qxd_mscg(lat, sigmas, x_ptrs, b_ptr, params: qxd_mscg_params, stream=0):
+    """Returns (status, info, per-shift true relative residuals); status
+    QXD_ERR_NOT_CONVERGED does not raise."""
+    n = len(sigmas)
+    info = qxd_mscg_info()
+    rel = (_d * n)()
+    rc = _call("qxd_mscg", lat, n, (_d * n)(*sigmas), (_vp * n)(*x_ptrs), b_ptr, ctypes.byref(params),
+               ctypes.byref(info), rel, stream)
+    if rc not in (QXD_OK, QXD_ERR_NOT_CONVERGED):
+        check(rc)
+    return rc, info, list(rel)
+
+
+def qxd_rational_apply(lat, nu, mu, out_ptr, phi_ptr, params: qxd_mscg_params, stream=0):
+    """Returns (status, info); status QXD_ERR_NOT_CONVERGED does not raise."""
+    n = len(nu)
+    if len(mu) != n:
+        raise ValueError("nu and mu must have the same length")
+    info = qxd_mscg_info()
+    rc = _call("qxd_rational_apply", lat, n, (_d * n)(*nu), (_d * n)(*mu), out_ptr, phi_ptr,
+               ctypes.byref(params), ctypes.byref(info), stream)
     if rc not in (QXD_OK, QXD_ERR_NOT_CONVERGED):
         check(rc)
     return rc, info
@@ -353,6 +414,41 @@ class Lattice:
         if b.device.type == "cpu":
             p.flags |= QXD_HOST
         rc, info = qxd_solve(self.handle, x.data_ptr(), b.data_ptr(), p, _stream_ptr(stream))
+        return rc, info.as_dict()
+
+    def sw_logdet(self, sites=QXD_SITES_ODD) -> float:
+        """sum of ln|det M(x)| over the selected sites (odd: ln|Det D_oo|)."""
+        return qxd_sw_logdet(self.handle, sites)
+
+    @staticmethod
+    def _mscg_params(fields, native, host, kw):
+        p = qxd_mscg_defaults()
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown multi-shift CG parameter {k}")
+            setattr(p, k, v)
+        if native:
+            p.flags |= QXD_LAYOUT_NATIVE
+        if host:
+            p.flags |= QXD_HOST
+        return p
+
+    def mscg(self, xs, b, sigmas, native=False, stream=None, **kw):
+        """xs[j] = (D_hat^dag D_hat + sigmas[j])^-1 b on the even sites (FP64
+        complex128 full-lattice tensors). Returns (status, info dict, relres list)."""
+        if len(xs) != len(sigmas):
+            raise ValueError("one solution tensor per shift")
+        p = self._mscg_params(None, native, b.device.type == "cpu", kw)
+        rc, info, rel = qxd_mscg(self.handle, list(sigmas), [x.data_ptr() for x in xs], b.data_ptr(), p,
+                                 _stream_ptr(stream))
+        return rc, info.as_dict(), rel
+
+    def rational_apply(self, out, phi, nu, mu, native=False, stream=None, **kw):
+        """out = prod_j (A + nu_j^2)/(A + mu_j^2) phi, A = D_hat^dag D_hat.
+        Returns (status, info dict); info['action'] = Re <phi, out>."""
+        p = self._mscg_params(None, native, phi.device.type == "cpu", kw)
+        rc, info = qxd_rational_apply(self.handle, list(nu), list(mu), out.data_ptr(), phi.data_ptr(), p,
+                                      _stream_ptr(stream))
         return rc, info.as_dict()
 
     def pack(self, native_out, lex_in, prec, stream=None):

@@ -60,3 +60,19 @@ def test_null_arguments_are_errors():
     assert lib.qxd_sw_build(None) == qxd.QXD_ERR_ARG
     assert lib.qxd_lattice_destroy(None) == qxd.QXD_OK
     assert "NULL" in qxd.qxd_last_error() or qxd.qxd_last_error() != ""
+
+
+def test_pseudofermion_entry_points_check_arguments():
+    lib = qxd.lib()
+    out = ctypes.c_double()
+    assert lib.qxd_sw_logdet(None, qxd.QXD_SITES_ODD, ctypes.byref(out)) == qxd.QXD_ERR_ARG
+    p = qxd.qxd_mscg_defaults()
+    assert (p.tol, p.max_iter, p.flags) == (1e-10, 10000, 0)
+    info = qxd.qxd_mscg_info()
+    sig = (ctypes.c_double * 1)(0.1)
+    xs = (ctypes.c_void_p * 1)(None)
+    assert lib.qxd_mscg(None, 1, sig, xs, None, ctypes.byref(p), ctypes.byref(info), None, None) == \
+        qxd.QXD_ERR_ARG
+    assert info.status == qxd.QXD_ERR_ARG
+    assert lib.qxd_rational_apply(None, 1, sig, sig, None, None, ctypes.byref(p), ctypes.byref(info),
+                                  None) == qxd.QXD_ERR_ARG
