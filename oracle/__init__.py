@@ -5,3 +5,4 @@ from .qxd_oracle import (CHARGE_C, CHARGE_C_INV, GAMMA, GAMMA5, PAULI, Dirac,  #
 from .qxd_rhmc import (D_hat_dagger, cg, gamma5_mul, ln_abs_det_blocks,  # noqa: F401
                        ln_abs_det_Doo, normal_apply, pf_action_term, rational_apply,
                        shifted_solve)
+from . import qxd_flow, qxd_rhmc  # noqa: F401
