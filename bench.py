@@ -669,6 +669,48 @@ def rational_benchmark(qxd, torch):
             "bytes_per_even_site_per_iteration": MSCG_BYTES_FIXED + len(mu) * MSCG_BYTES_PER_SHIFT}
 
 
+# Wilson flow of the solver workload's gauge field: FP64 work per RK3 stage
+# and integrated link (staple sum 12 products, W = U S, exp by 10 Horner
+# products, exp(X) U: 24 complex 3x3 products of 198 flops, plus the U(1)
+# angle update), the links integrated being the physical ones (half the
+# simulated lattice with C* boundaries)
+FLOW_WORKLOAD = dict(eps=0.02, steps=(5, 5, 10), q_el=1.0 / 6.0)
+FLOW_FLOPS_PER_LINK_STAGE = 24 * 198 + 60
+
+
+def flow_benchmark(qxd, torch):
+    """Wilson flow to t = 0.4 in stages, timing each call; observables at
+    every stage."""
+    w = SOLVE_WORKLOAD
+    F = FLOW_WORKLOAD
+    su3, ang, psi, V = make_inputs("cuda", w)
+    del psi
+    lat = qxd.Lattice(w["T"], w["L1"], w["L2"], w["L3"], w["mask"])
+    lat.set_gauge(su3, ang)
+    del su3, ang
+    lat.wflow(F["eps"], 1)  # warm-up (and t = eps)
+    t = F["eps"]
+    rows = [{"t": t, "obs": lat.gauge_observables(F["q_el"])}]
+    ms_per_step = []
+    for n in F["steps"]:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.wflow(F["eps"], n)
+        dt = time.perf_counter() - t0
+        t += n * F["eps"]
+        ms_per_step.append(dt * 1e3 / n)
+        rows.append({"t": round(t, 6), "ms_per_step": dt * 1e3 / n, "obs": lat.gauge_observables(F["q_el"])})
+    lat.close()
+    links = 4 * V // 2
+    flops_step = 3 * links * FLOW_FLOPS_PER_LINK_STAGE
+    best = min(ms_per_step)
+    return {"workload": "Wilson flow (Luscher RK3, SU(3) and compact U(1)), doubled 64x64x32x32 C* lattice "
+                        "(L=32, T=64), eps 0.02, FP64; obs = (E_SU(3), E_U(1) at q_el=1/6, Q_top)",
+            "stages": rows, "ms_per_rk3_step": best,
+            "fp64_tflops_model": flops_step / (best / 1e3) / 1e12,
+            "flops_per_rk3_step_model": flops_step}
+
+
 def sap_benchmark(qxd, torch, steps, w):
     """Time one FP32 SAP application (ncy 5, nmr 5) on the lattice of workload w."""
     su3, ang, psi, V = make_inputs("cuda", w)
@@ -779,10 +821,11 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="dw", choices=["dw", "solve", "sap", "batch", "serve", "rational"],
+    ap.add_argument("--mode", default="dw", choices=["dw", "solve", "sap", "batch", "serve", "rational", "flow"],
                     help="dw: the Dw throughput line (plus a solver summary unless --no-solve); "
                          "solve: solver comparison only; sap: time the SAP preconditioner only; "
-                         "batch / serve: multi-RHS and serving workloads; rational: pseudofermion action")
+                         "batch / serve: multi-RHS and serving workloads; rational: pseudofermion action; "
+                         "flow: Wilson flow and gauge observables")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--write-traffic", metavar="NCU_CSV",
                     help="write profiles/dirac_fp32_q2_traffic.json from an ncu CSV of k_dirac launches and exit")
@@ -806,8 +849,10 @@ def main():
     ge.build()
     from paper_1710_08839_gb300 import qxd
 
-    if args.mode in ("solve", "sap", "batch", "serve", "rational"):
-        if args.mode == "solve":
+    if args.mode in ("solve", "sap", "batch", "serve", "rational", "flow"):
+        if args.mode == "flow":
+            res = flow_benchmark(qxd, torch)
+        elif args.mode == "solve":
             res = solve_benchmark(qxd, torch)
         elif args.mode == "rational":
             res = rational_benchmark(qxd, torch)

@@ -385,6 +385,47 @@ int qxd_mscg(qxd_lattice* lat, int nshift, const double* sigma, void* const* x, 
 int qxd_rational_apply(qxd_lattice* lat, int n, const double* nu, const double* mu, void* out, const void* phi,
                        const qxd_mscg_params* params, qxd_mscg_info* info, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Gauge observables and the Wilson flow (App. A; the paper defines its
+ * action densities and topological charge at positive flow time of the
+ * Wilson flow of Luscher (2010), Sec. 3). FP64.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * out[0] = E_SU(3) = -1/(2V) sum_x sum_{mu,nu} tr{F_munu(x) F_munu(x)}
+ * out[1] = E_U(1)  = -1/(2V) sum_x sum_{mu,nu} A_munu(x)^2
+ * out[2] = Q_top   = 1/(32 pi^2) sum_x sum eps_{mu nu rho sigma} tr{F_munu F_rhosigma}
+ * with the clover tensors of the SW term: F = (Q_munu - Q_numu)/8 and
+ * A_munu = i/(4 q_el) Im{four U(1) plaquettes} (Sec. 2.3). Both tensors are
+ * anti-Hermitian, so the minus signs (not printed in the paper) make the E
+ * non-negative. Sums run over the physical lattice of volume V: with C*
+ * boundaries the mirror half holds the conjugate field with the same
+ * densities, so E is the mean over the simulated lattice and Q half its sum.
+ * q_el > 0 is the elementary charge of the U(1) normalisation (1/6 with C*
+ * boundaries in the paper, Sec. 2.2). Works on a lattice or a view (the
+ * gauge field of the owner). Synchronises the lattice's stream.
+ */
+int qxd_gauge_observables(qxd_lattice* lat, double q_el, double* out);
+
+/*
+ * Flows the lattice's gauge field in place by nsteps steps of size eps
+ * (flow time t = nsteps eps): SU(3) by dV/dt = Z(V) V with
+ * Z(x,mu) = -1/2 (W - W^dag) + 1/6 tr(W - W^dag), W = U(x,mu) times the sum
+ * of the six staples (Luscher's Wilson flow), integrated with his
+ * third-order Runge-Kutta scheme; the U(1) angles by the same scheme with
+ * dA(x,mu)/dt = -sum_{nu != mu} [sin theta_munu(x) - sin theta_munu(x-nu)]
+ * (compact plaquette action), kept in [-pi, pi). With C* boundaries only the
+ * physical links are integrated and the mirror links are set to their
+ * complex conjugates (-A), so the field stays admissible exactly.
+ * Afterwards the FP32 copies and the field tensors are refreshed, and every
+ * clover term built from the old field (this lattice's and its views') is
+ * stale: qxd_Dw and the solvers return QXD_ERR_STATE until qxd_sw_build.
+ * Views cannot flow (QXD_ERR_STATE): flow the lattice that owns the field.
+ * Allocates its work fields (about 0.9 KB per site) for the call.
+ * Synchronises the lattice's stream.
+ */
+int qxd_wflow(qxd_lattice* lat, double eps, int nsteps);
+
 /* Bytes of one spinor field in the native layout for precision `prec`. */
 size_t qxd_spinor_bytes(const qxd_lattice* lat, int prec);
 

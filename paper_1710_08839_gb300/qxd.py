@@ -122,6 +122,8 @@ SIGNATURES = {
                       ctypes.POINTER(qxd_mscg_info), ctypes.POINTER(_d), _vp]),
     "qxd_rational_apply": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), _vp, _vp,
                                 ctypes.POINTER(qxd_mscg_params), ctypes.POINTER(qxd_mscg_info), _vp]),
+    "qxd_gauge_observables": (_i, [_vp, _d, ctypes.POINTER(_d)]),
+    "qxd_wflow": (_i, [_vp, _d, _i]),
     "qxd_spinor_bytes": (ctypes.c_size_t, [_vp, _i]),
     "qxd_spinor_pack": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_spinor_unpack": (_i, [_vp, _vp, _vp, _i, _vp]),
@@ -230,6 +232,17 @@ def qxd_sw_logdet(lat, sites) -> float:
     out = _d()
     check(_call("qxd_sw_logdet", lat, sites, ctypes.byref(out)))
     return out.value
+
+
+def qxd_gauge_observables(lat, q_el):
+    """(E_SU(3), E_U(1), Q_top) of the lattice's gauge field."""
+    out = (_d * 3)()
+    check(_call("qxd_gauge_observables", lat, q_el, out))
+    return tuple(out)
+
+
+def qxd_wflow(lat, eps, nsteps) -> int:
+    return check(_call("qxd_wflow", lat, eps, nsteps))
 
 
 def qxd_mscg_defaults() -> qxd_mscg_params:
@@ -415,6 +428,15 @@ class Lattice:
             p.flags |= QXD_HOST
         rc, info = qxd_solve(self.handle, x.data_ptr(), b.data_ptr(), p, _stream_ptr(stream))
         return rc, info.as_dict()
+
+    def gauge_observables(self, q_el):
+        """(E_SU(3), E_U(1), Q_top) of the gauge field (App. A)."""
+        return qxd_gauge_observables(self.handle, q_el)
+
+    def wflow(self, eps, nsteps):
+        """Wilson flow of the gauge field to t = nsteps * eps (in place);
+        the clover term must be rebuilt afterwards."""
+        qxd_wflow(self.handle, eps, nsteps)
 
     def sw_logdet(self, sites=QXD_SITES_ODD) -> float:
         """sum of ln|det M(x)| over the selected sites (odd: ln|Det D_oo|)."""
