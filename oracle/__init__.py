@@ -6,3 +6,4 @@ from .qxd_rhmc import (D_hat_dagger, cg, gamma5_mul, ln_abs_det_blocks,  # noqa:
                        ln_abs_det_Doo, normal_apply, pf_action_term, rational_apply,
                        shifted_solve)
 from . import qxd_flow, qxd_rhmc  # noqa: F401
+from . import qxd_dfl  # noqa: F401
