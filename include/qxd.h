@@ -195,9 +195,15 @@ int qxd_sap(qxd_lattice* lat, void* out, const void* in, int ncy, int nmr, int f
  * system QXD_SOLVE_EO:   GCR on D_hat for x_e, then x_o by reconstruction.
  * precond QXD_PRECOND_SAP: Schwarz alternating procedure on 4^4 blocks
  * (full system only; inner_prec FP32 or FP64).
+ * precond QXD_PRECOND_DFL_SAP: local deflation plus SAP (full system,
+ * inner_prec FP32; needs qxd_dfl_subspace, or qxd_dfl_refresh after the
+ * operator changed): phi = chi + SAP(r - D chi), chi = P A^-1 P^dag r with the
+ * little system A solved by GCR to a relative residual dfl_tol (at most
+ * dfl_max_iter steps).
  * ------------------------------------------------------------------------- */
 #define QXD_PRECOND_NONE 0
 #define QXD_PRECOND_SAP 1
+#define QXD_PRECOND_DFL_SAP 2
 #define QXD_SOLVE_FULL 0
 #define QXD_SOLVE_EO 1
 
@@ -212,6 +218,8 @@ typedef struct {
     int sap_nmr;      /* minimal-residual steps per block solve                      */
     double delta;     /* reliable update when |r_inner| < delta |r_true| (0: off)    */
     int flags;        /* x and b: QXD_DEVICE | QXD_HOST, QXD_LAYOUT_LEX | _NATIVE     */
+    double dfl_tol;   /* QXD_PRECOND_DFL_SAP: relative residual of the little solves */
+    int dfl_max_iter; /* QXD_PRECOND_DFL_SAP: step limit of one little solve         */
 } qxd_solver_params;
 
 typedef struct {
@@ -222,10 +230,12 @@ typedef struct {
     double time_ms;        /* wall time of the call                                 */
     int dw64_calls;        /* FP64 applications of D (or D_hat)                     */
     int inner_calls;       /* applications of the inner operator                    */
+    int little_iters;      /* little-solver steps over all preconditioner calls     */
 } qxd_solve_info;
 
 /* Defaults: tol 1e-10, max_iter 2000, nkv 16, no preconditioner, full system,
- * FP64, ncy 5, nmr 5, delta 1e-4, device lexicographic buffers. */
+ * FP64, ncy 5, nmr 5, delta 1e-4, device lexicographic buffers, dfl_tol 1e-2,
+ * dfl_max_iter 64. */
 void qxd_solver_defaults(qxd_solver_params* p);
 
 /*
@@ -425,6 +435,55 @@ int qxd_gauge_observables(qxd_lattice* lat, double q_el, double* out);
  * Synchronises the lattice's stream.
  */
 int qxd_wflow(qxd_lattice* lat, double eps, int nsteps);
+
+/* ---------------------------------------------------------------------------
+ * Local deflation (openQ*D's deflation-accelerated solver, named in Sec. 1
+ * and Table 2 without details; Luscher's local deflation). The deflation
+ * subspace S is spanned by block-local fields phi_{b,k}, k < ns, on the
+ * 4^4 blocks of the Schwarz method: ns global fields restricted to each
+ * block and orthonormalised there in order (Gram-Schmidt). The little
+ * operator A_{(b,k),(b',l)} = <phi_{b,k}, D phi_{b',l}> couples each block to
+ * itself and its 8 neighbours. Subspace and little operator belong to the
+ * lattice (or view) they were built on; FP32 storage. The lattice must admit
+ * the SAP blocks (as qxd_sap).
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Builds S from ns seeded Gaussian fields, each passed niter times through
+ * the Schwarz method (ncy cycles, 4 MR steps: inverse iteration towards the
+ * low modes) with a block orthonormalisation after every pass, then the
+ * little operator of the current D. 1 <= ns <= 64. Needs qxd_sw_build.
+ * Returns QXD_ERR_NUMERIC if a block's fields became linearly dependent.
+ * Memory: ns * 96 + 600 bytes per site, plus the little operator
+ * (9 ns^2 * 8 bytes per block). Synchronises the lattice's stream.
+ */
+int qxd_dfl_subspace(qxd_lattice* lat, int ns, int niter, int ncy, unsigned long long seed);
+
+/*
+ * Builds S from ns given fields psi[k] (FP64 device fields, lexicographic
+ * layout; they are block-orthonormalised, not modified) and the little
+ * operator of the current D. Errors as qxd_dfl_subspace.
+ */
+int qxd_dfl_set_basis(qxd_lattice* lat, int ns, const void* const* psi);
+
+/*
+ * Recomputes the little operator for the lattice's current operator (after
+ * qxd_set_params + qxd_sw_build with a new mass or charge, or a new gauge
+ * field) keeping the subspace. QXD_ERR_STATE without a subspace or clover.
+ */
+int qxd_dfl_refresh(qxd_lattice* lat);
+
+/*
+ * Copies the little operator to host memory: A_out[((b * 9 + j) * ns + k) * ns
+ * + l] (complex, re/im pairs of doubles) = <phi_{b,k}, D phi_{n_j(b),l}>,
+ * n_0(b) = b, n_{1+2mu}(b) = b + mu, n_{2+2mu}(b) = b - mu, blocks numbered
+ * lexicographically in block coordinates (b3 fastest). A_out may be NULL to
+ * query *ns_out and *nblk_out only.
+ */
+int qxd_dfl_little(qxd_lattice* lat, double* A_out, int* ns_out, int* nblk_out);
+
+/* Writes sum_b phi_{b,k} (FP64 device field, lexicographic layout) to out. */
+int qxd_dfl_basis(qxd_lattice* lat, int k, void* out);
 
 /* Bytes of one spinor field in the native layout for precision `prec`. */
 size_t qxd_spinor_bytes(const qxd_lattice* lat, int prec);

@@ -141,6 +141,7 @@ int qxd_lattice_destroy(qxd_lattice* lat) {
     if (lat->parent) --lat->parent->nviews;
     release_solver(lat);
     release_mscg(lat);
+    release_dfl(lat);
     free_all(lat);
     delete lat;
     return QXD_OK;
@@ -272,6 +273,7 @@ int qxd_sw_build(qxd_lattice* lat) {
                                                     " clover blocks are singular or not finite");
     lat->has_clover = true;
     lat->built_gauge_version = gauge_owner(lat)->gauge_version;
+    ++lat->op_version;
     return QXD_OK;
 }
 

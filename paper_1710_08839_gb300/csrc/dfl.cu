@@ -1,0 +1,666 @@
+// Local deflation of the SAP-preconditioned GCR solver (openQ*D's
+// deflation-accelerated solver, named in Sec. 1 and Table 2; Luscher's local
+// deflation).
+//
+// * Subspace: Ns global FP32 fields psi_k, smoothed by SAP applications
+//   (inverse iteration on the low modes), each pass followed by block-wise
+//   orthonormalisation on the 4^4 blocks of the Schwarz method: the fields
+//   restricted to a block are orthonormalised in order (modified
+//   Gram-Schmidt), giving phi_{b,k}; phi_k = sum_b phi_{b,k} is stored as one
+//   native FP32 field.
+// * Little operator: A_{b,j}[k][l] = <phi_{b,k}, D phi_{n_j(b),l}> for
+//   n_0(b) = b and n_{1+2mu}(b) = b + mu, n_{2+2mu}(b) = b - mu (block
+//   neighbours; across a shifted C* boundary the block coordinate b1 moves by
+//   L1/4 like the sites). For each l: T = D phi_l (the FP32 operator) and the
+//   hop of every face site out of its block (H_mu), then per block and k the
+//   projections <phi_{b,k}, T>_b and <phi_{b,k}, H_mu>_face give
+//   A_{b,b+-mu} directly and A_{b,b} = <phi_{b,k}, T>_b - sum of the faces.
+// * Preconditioner: M eta = chi + M_SAP(eta - D chi), chi = P A^-1 P^dag eta,
+//   with the little system solved by GCR to a relative residual dfl_tol.
+#include <chrono>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "blas.cuh"
+#include "dfl.cuh"
+#include "dirac_common.cuh"
+#include "solver.cuh"
+
+namespace qxd {
+
+namespace {
+
+constexpr int BS = 4;        // block size (the Schwarz blocks)
+constexpr int BSITES = 256;  // sites per block = threads per block of the kernels below
+
+// block b (lexicographic in block coordinates, B3 fastest) and local site t
+// (lexicographic in the block, x3 fastest) -> global coordinates
+__device__ __forceinline__ void block_site(const Geom& g, const DflGeom& d, int b, int t, int x[4]) {
+    int B3 = b % d.nb[3];
+    int r = b / d.nb[3];
+    int B2 = r % d.nb[2];
+    r /= d.nb[2];
+    int B1 = r % d.nb[1];
+    int B0 = r / d.nb[1];
+    x[0] = BS * B0 + ((t >> 6) & 3);
+    x[1] = BS * B1 + ((t >> 4) & 3);
+    x[2] = BS * B2 + ((t >> 2) & 3);
+    x[3] = BS * B3 + (t & 3);
+}
+
+__device__ __forceinline__ int native_at(const Geom& g, const int x[4]) {
+    return native_index(g, lex_index(g, x[0], x[1], x[2], x[3]), (x[0] + x[1] + x[2] + x[3]) & 1);
+}
+
+// neighbour block of b in direction mu (dir = +1 or -1)
+__device__ __forceinline__ int block_nbr(const Geom& g, const DflGeom& d, int b, int mu, int dir) {
+    int B[4];
+    B[3] = b % d.nb[3];
+    int r = b / d.nb[3];
+    B[2] = r % d.nb[2];
+    r /= d.nb[2];
+    B[1] = r % d.nb[1];
+    B[0] = r / d.nb[1];
+    int v = B[mu] + dir;
+    const bool crossed = v < 0 || v >= d.nb[mu];
+    B[mu] = (v + d.nb[mu]) % d.nb[mu];
+    if (crossed && ((mu == 2 && g.cs2) || (mu == 3 && g.cs3))) B[1] = (B[1] + g.L1 / BS) % d.nb[1];
+    return ((B[0] * d.nb[1] + B[1]) * d.nb[2] + B[2]) * d.nb[3] + B[3];
+}
+
+// conj(a) . b over 12 complex numbers
+__device__ __forceinline__ void cdot12(const cplx<float> a[12], const cplx<float> b[12], double& re, double& im) {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        re += (double)a[i].re * b[i].re + (double)a[i].im * b[i].im;
+        im += (double)a[i].re * b[i].im - (double)a[i].im * b[i].re;
+    }
+}
+
+// block-wide sum of NV doubles (BSITES threads); result valid in every thread
+template <int NV>
+__device__ __forceinline__ void block_sum(double v[NV], double* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+        double x = v[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[warp * NV + c] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+        double x = 0.0;
+        for (int w = 0; w < BSITES / 32; ++w) x += sh[w * NV + c];
+        v[c] = x;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// random fields and block orthonormalisation
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Gaussian FP32 entries (Box-Muller on two 24-bit uniforms per complex entry)
+__global__ void k_dfl_random(size_t n, unsigned long long seed, float2* __restrict__ out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const unsigned long long h = splitmix64(seed ^ splitmix64(i));
+        const float u1 = ((float)(h >> 40) + 1.0f) * (1.0f / 16777217.0f);
+        const float u2 = (float)((h >> 16) & 0xFFFFFF) * (1.0f / 16777216.0f);
+        const float rr = sqrtf(-2.0f * logf(u1));
+        float sn, cs;
+        sincospif(2.0f * u2, &sn, &cs);
+        out[i] = make_float2(rr * cs, rr * sn);
+    }
+}
+
+// modified Gram-Schmidt of the ns fields restricted to each block; bad[0]
+// counts blocks where a field became (numerically) dependent
+__global__ void __launch_bounds__(BSITES) k_dfl_orth(Geom g, DflGeom d, int ns, float4* __restrict__ basis,
+                                                     int* __restrict__ bad) {
+    __shared__ double sh[(BSITES / 32) * 2];
+    const int b = blockIdx.x;
+    int x[4];
+    block_site(g, d, b, threadIdx.x, x);
+    const int s = native_at(g, x);
+    const size_t V = (size_t)g.V;
+    for (int k = 0; k < ns; ++k) {
+        cplx<float> v[12];
+        load_spinor(basis + (size_t)k * 6 * V, g.V, s, v);
+        for (int l = 0; l < k; ++l) {
+            cplx<float> u[12];
+            load_spinor(basis + (size_t)l * 6 * V, g.V, s, u);
+            double c[2] = {0.0, 0.0};
+            cdot12(u, v, c[0], c[1]);
+            block_sum<2>(c, sh);
+            const float cr = (float)c[0], ci = (float)c[1];
+#pragma unroll
+            for (int i = 0; i < 12; ++i)
+                v[i] = mk(v[i].re - (cr * u[i].re - ci * u[i].im), v[i].im - (cr * u[i].im + ci * u[i].re));
+        }
+        double n2[1] = {0.0};
+#pragma unroll
+        for (int i = 0; i < 12; ++i) n2[0] += (double)v[i].re * v[i].re + (double)v[i].im * v[i].im;
+        block_sum<1>(n2, sh);
+        const bool ok = n2[0] > 1e-30 && isfinite(n2[0]);
+        const float inv = ok ? (float)(1.0 / sqrt(n2[0])) : 0.0f;
+        if (!ok && threadIdx.x == 0) atomicAdd(bad, 1);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) v[i] = mk(v[i].re * inv, v[i].im * inv);
+        store_spinor(basis + (size_t)k * 6 * V, g.V, s, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// little operator
+// ---------------------------------------------------------------------------
+
+// one hop of direction MU, DIR = +1 (forward) or -1 (backward), raw (without
+// the factor -1/2) as a full spinor: (1 -+ g_mu) W psi(x +- mu)
+template <bool QNZ, int MU, int DIR>
+__device__ __forceinline__ void dfl_hop(const Geom& g, const Fields<float>& f, const float4* __restrict__ psi,
+                                        float q, int x0, int x1, int x2, int x3, int s, int po,
+                                        cplx<float> out[12]) {
+    cplx<float> v[12], h0[3], h1[3], g0[3], g1[3], u[3][3];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) out[i] = mk(0.f, 0.f);
+    const int sn = native_index(g, neighbour_lex<MU, DIR>(g, x0, x1, x2, x3), po);
+    load_spinor(psi, g.V, sn, v);
+    project<float, MU, DIR>(v, h0, h1);
+    if (DIR > 0) {
+        load_link(f.U, g.V, MU, s, u);
+        su3_mul(u, h0, g0);
+        su3_mul(u, h1, g1);
+        if (QNZ) {
+            cplx<float> ph = link_phase(f.A, g.V, MU, s, q);
+            times3(ph, g0);
+            times3(ph, g1);
+        }
+    } else {
+        load_link(f.U, g.V, MU, sn, u);
+        su3_dag_mul(u, h0, g0);
+        su3_dag_mul(u, h1, g1);
+        if (QNZ) {
+            cplx<float> ph = conj(link_phase(f.A, g.V, MU, sn, q));
+            times3(ph, g0);
+            times3(ph, g1);
+        }
+    }
+    accumulate<float, MU, DIR>(out, g0, g1);
+}
+
+template <bool QNZ, int MU>
+__device__ __forceinline__ void face_hop(const Geom& g, const Fields<float>& f, const float4* psi, float q,
+                                         const int x[4], int s, int po, float4* __restrict__ H) {
+    const int l = x[MU] & (BS - 1);
+    cplx<float> h[12];
+    if (l == BS - 1) dfl_hop<QNZ, MU, +1>(g, f, psi, q, x[0], x[1], x[2], x[3], s, po, h);
+    else if (l == 0) dfl_hop<QNZ, MU, -1>(g, f, psi, q, x[0], x[1], x[2], x[3], s, po, h);
+    else {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) h[i] = mk(0.f, 0.f);
+    }
+    // the factor -1/2 of the hopping term
+#pragma unroll
+    for (int i = 0; i < 12; ++i) h[i] = mk(-0.5f * h[i].re, -0.5f * h[i].im);
+    store_spinor(H + (size_t)MU * 6 * g.V, g.V, s, h);
+}
+
+// H_mu(x) = the hop of direction mu that leaves the block of x (zero when x
+// is not on a face of direction mu), for all four mu
+template <bool QNZ>
+__global__ void __launch_bounds__(256) k_dfl_faces(Geom g, Fields<float> f, const float4* __restrict__ psi, float q,
+                                                   float4* __restrict__ H) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    int x[4];
+    native_coords(g, s, x[0], x[1], x[2], x[3]);
+    const int po = 1 - ((x[0] + x[1] + x[2] + x[3]) & 1);
+    face_hop<QNZ, 0>(g, f, psi, q, x, s, po, H);
+    face_hop<QNZ, 1>(g, f, psi, q, x, s, po, H);
+    face_hop<QNZ, 2>(g, f, psi, q, x, s, po, H);
+    face_hop<QNZ, 3>(g, f, psi, q, x, s, po, H);
+}
+
+// A[b][j][k][l] for one l: projections of T = D phi_l and of the face hops
+__global__ void __launch_bounds__(BSITES) k_dfl_project(Geom g, DflGeom d, int ns, int l,
+                                                        const float4* __restrict__ basis,
+                                                        const float4* __restrict__ T,
+                                                        const float4* __restrict__ H, float2* __restrict__ A) {
+    __shared__ double sh[(BSITES / 32) * 18];
+    const int b = blockIdx.x;
+    int x[4];
+    block_site(g, d, b, threadIdx.x, x);
+    const int s = native_at(g, x);
+    const size_t V = (size_t)g.V;
+    cplx<float> t[12];
+    load_spinor(T, g.V, s, t);
+    for (int k = 0; k < ns; ++k) {
+        cplx<float> u[12];
+        load_spinor(basis + (size_t)k * 6 * V, g.V, s, u);
+        double c[18];
+#pragma unroll
+        for (int i = 0; i < 18; ++i) c[i] = 0.0;
+        cdot12(u, t, c[0], c[1]);
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const int lm = x[mu] & (BS - 1);
+            if (lm == BS - 1 || lm == 0) {
+                cplx<float> h[12];
+                load_spinor(H + (size_t)mu * 6 * V, g.V, s, h);
+                const int j = lm == BS - 1 ? 1 + 2 * mu : 2 + 2 * mu;
+                double re = 0.0, im = 0.0;
+                cdot12(u, h, re, im);
+                c[2 * j] += re;
+                c[2 * j + 1] += im;
+            }
+        }
+        block_sum<18>(c, sh);
+        if (threadIdx.x == 0) {
+            double dre = c[0], dim = c[1];
+            for (int j = 1; j < 9; ++j) {
+                dre -= c[2 * j];
+                dim -= c[2 * j + 1];
+                A[(((size_t)b * 9 + j) * ns + k) * ns + l] = make_float2((float)c[2 * j], (float)c[2 * j + 1]);
+            }
+            A[(((size_t)b * 9 + 0) * ns + k) * ns + l] = make_float2((float)dre, (float)dim);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// restriction, prolongation, little operator
+// ---------------------------------------------------------------------------
+
+// c[b][k] = <phi_{b,k}, eta>_b
+__global__ void __launch_bounds__(BSITES) k_dfl_restrict(Geom g, DflGeom d, int ns, const float4* __restrict__ basis,
+                                                         const float4* __restrict__ eta, double2* __restrict__ c) {
+    __shared__ double sh[(BSITES / 32) * 2];
+    const int b = blockIdx.x;
+    int x[4];
+    block_site(g, d, b, threadIdx.x, x);
+    const int s = native_at(g, x);
+    cplx<float> e[12];
+    load_spinor(eta, g.V, s, e);
+    for (int k = 0; k < ns; ++k) {
+        cplx<float> u[12];
+        load_spinor(basis + (size_t)k * 6 * g.V, g.V, s, u);
+        double v[2] = {0.0, 0.0};
+        cdot12(u, e, v[0], v[1]);
+        block_sum<2>(v, sh);
+        if (threadIdx.x == 0) c[(size_t)b * ns + k] = make_double2(v[0], v[1]);
+    }
+}
+
+// out(x) = sum_k c[b(x)][k] phi_k(x)
+__global__ void __launch_bounds__(BSITES) k_dfl_prolong(Geom g, DflGeom d, int ns, const float4* __restrict__ basis,
+                                                        const double2* __restrict__ c, float4* __restrict__ out) {
+    const int b = blockIdx.x;
+    int x[4];
+    block_site(g, d, b, threadIdx.x, x);
+    const int s = native_at(g, x);
+    float acc[24];
+#pragma unroll
+    for (int i = 0; i < 24; ++i) acc[i] = 0.f;
+    for (int k = 0; k < ns; ++k) {
+        const double2 ck = c[(size_t)b * ns + k];
+        const float cr = (float)ck.x, ci = (float)ck.y;
+        cplx<float> u[12];
+        load_spinor(basis + (size_t)k * 6 * g.V, g.V, s, u);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {
+            acc[2 * i] += cr * u[i].re - ci * u[i].im;
+            acc[2 * i + 1] += cr * u[i].im + ci * u[i].re;
+        }
+    }
+    cplx<float> w[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) w[i] = mk(acc[2 * i], acc[2 * i + 1]);
+    store_spinor(out, g.V, s, w);
+}
+
+// out[b][k] = sum_j sum_l A[b][j][k][l] in[n_j(b)][l]; one thread per (b, k)
+__global__ void k_dfl_little_apply(Geom g, DflGeom d, int ns, const float2* __restrict__ A,
+                                   const double2* __restrict__ in, double2* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.nblk * ns) return;
+    const int b = i / ns, k = i - b * ns;
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j < 9; ++j) {
+        const int nb = j == 0 ? b : block_nbr(g, d, b, (j - 1) >> 1, (j & 1) ? +1 : -1);
+        const float2* a = A + (((size_t)b * 9 + j) * ns + k) * ns;
+        const double2* v = in + (size_t)nb * ns;
+        for (int l = 0; l < ns; ++l) {
+            const float2 al = a[l];
+            const double2 vl = v[l];
+            re += (double)al.x * vl.x - (double)al.y * vl.y;
+            im += (double)al.x * vl.y + (double)al.y * vl.x;
+        }
+    }
+    out[i] = make_double2(re, im);
+}
+
+__global__ void k_f32_to_f64_native(int V, const float4* __restrict__ in, double2* __restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    cplx<float> v[12];
+    load_spinor(in, V, s, v);
+    cplx<double> w[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) w[i] = mk((double)v[i].re, (double)v[i].im);
+    store_spinor(out, V, s, w);
+}
+
+int dalloc_bytes(void** p, size_t bytes, const char* what) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, what);
+    }
+    return QXD_OK;
+}
+
+}  // namespace
+
+void DflWork::release() {
+    void* ps[] = {basis, A, chi, tfield, H, lx, lr, lc, d_bad};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    for (int k = 0; k < DFL_NKV; ++k) {
+        if (lp[k]) cudaFree(lp[k]);
+        if (lq[k]) cudaFree(lq[k]);
+        lp[k] = lq[k] = nullptr;
+    }
+    basis = nullptr;
+    A = nullptr;
+    chi = tfield = H = nullptr;
+    lx = lr = lc = nullptr;
+    d_bad = nullptr;
+    red.release();
+    ns = 0;
+    ready = false;
+}
+
+int DflWork::ensure(const Geom& g, int ns_) {
+    if (ns == ns_ && basis) return QXD_OK;
+    release();
+    d.nb[0] = g.N0 / BS;
+    d.nb[1] = g.N1 / BS;
+    d.nb[2] = g.N2 / BS;
+    d.nb[3] = g.N3 / BS;
+    d.nblk = d.nb[0] * d.nb[1] * d.nb[2] * d.nb[3];
+    const size_t V = (size_t)g.V;
+    const size_t nl = (size_t)d.nblk * ns_;
+    int rc;
+    if ((rc = dalloc_bytes((void**)&basis, (size_t)ns_ * 6 * V * sizeof(float4), "cudaMalloc(deflation basis)")) ||
+        (rc = dalloc_bytes((void**)&A, (size_t)d.nblk * 9 * ns_ * ns_ * sizeof(float2), "cudaMalloc(little operator)")) ||
+        (rc = dalloc_bytes((void**)&chi, 6 * V * sizeof(float4), "cudaMalloc(deflation field)")) ||
+        (rc = dalloc_bytes((void**)&tfield, 6 * V * sizeof(float4), "cudaMalloc(deflation field)")) ||
+        (rc = dalloc_bytes((void**)&H, 4 * 6 * V * sizeof(float4), "cudaMalloc(deflation faces)")) ||
+        (rc = dalloc_bytes((void**)&lx, nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
+        (rc = dalloc_bytes((void**)&lr, nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
+        (rc = dalloc_bytes((void**)&lc, nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
+        (rc = dalloc_bytes((void**)&d_bad, sizeof(int), "cudaMalloc(deflation status)")))
+        return rc;
+    for (int k = 0; k < DFL_NKV; ++k)
+        if ((rc = dalloc_bytes((void**)&lp[k], nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
+            (rc = dalloc_bytes((void**)&lq[k], nl * sizeof(double2), "cudaMalloc(little vectors)")))
+            return rc;
+    if ((rc = red.init())) return rc;
+    ns = ns_;
+    return QXD_OK;
+}
+
+void release_dfl(qxd_lattice* lat) {
+    if (!lat->dfl) return;
+    lat->dfl->release();
+    delete lat->dfl;
+    lat->dfl = nullptr;
+}
+
+namespace {
+
+int orthonormalise(qxd_lattice* lat, DflWork& W, cudaStream_t st) {
+    QXD_CUDA(cudaMemsetAsync(W.d_bad, 0, sizeof(int), st));
+    k_dfl_orth<<<W.d.nblk, BSITES, 0, st>>>(lat->g, W.d, W.ns, W.basis, W.d_bad);
+    QXD_LAUNCHED("k_dfl_orth");
+    int bad = 0;
+    QXD_CUDA(cudaMemcpyAsync(&bad, W.d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    QXD_CUDA(cudaStreamSynchronize(st));
+    if (bad) return fail(QXD_ERR_NUMERIC, "deflation subspace: " + std::to_string(bad) +
+                                             " blocks with linearly dependent fields");
+    return QXD_OK;
+}
+
+int build_little(qxd_lattice* lat, DflWork& W, cudaStream_t st) {
+    const Geom& g = lat->g;
+    Fields<float> f{nullptr, nullptr, lat->U32, lat->A32, lat->C32};
+    const float q = (float)lat->qhat;
+    int rc;
+    for (int l = 0; l < W.ns; ++l) {
+        const float4* phil = W.basis + (size_t)l * 6 * g.V;
+        if ((rc = launch_dirac(lat, W.tfield, phil, QXD_FP32, st))) return rc;
+        if (lat->qhat != 0) k_dfl_faces<true><<<(g.V + 255) / 256, 256, 0, st>>>(g, f, phil, q, W.H);
+        else k_dfl_faces<false><<<(g.V + 255) / 256, 256, 0, st>>>(g, f, phil, q, W.H);
+        QXD_LAUNCHED("k_dfl_faces");
+        k_dfl_project<<<W.d.nblk, BSITES, 0, st>>>(g, W.d, W.ns, l, W.basis, W.tfield, W.H, W.A);
+        QXD_LAUNCHED("k_dfl_project");
+    }
+    QXD_CUDA(cudaStreamSynchronize(st));
+    W.op_version = lat->op_version;
+    W.ready = true;
+    (void)BSITES;
+    return QXD_OK;
+}
+
+int little_apply(qxd_lattice* lat, DflWork& W, double2* out, const double2* in, cudaStream_t st) {
+    const int n = W.d.nblk * W.ns;
+    k_dfl_little_apply<<<(n + 127) / 128, 128, 0, st>>>(lat->g, W.d, W.ns, W.A, in, out);
+    QXD_LAUNCHED("k_dfl_little_apply");
+    return QXD_OK;
+}
+
+// GCR on the little system A y = c (W.lc) into W.lx, to |r| <= tol |c| or
+// max_iter steps (restarted every DFL_NKV steps)
+int little_gcr(qxd_lattice* lat, DflWork& W, double tol, int max_iter, int* iters, cudaStream_t st) {
+    const size_t n = (size_t)W.d.nblk * W.ns;
+    const size_t bytes = n * sizeof(double2);
+    int rc;
+    double cc;
+    if ((rc = blas_norm2<double2>(W.red, n, W.lc, &cc, st))) return rc;
+    QXD_CUDA(cudaMemsetAsync(W.lx, 0, bytes, st));
+    *iters = 0;
+    if (cc == 0.0) return QXD_OK;
+    if (!std::isfinite(cc)) return fail(QXD_ERR_NUMERIC, "little solver: non-finite source");
+    const double target = tol * std::sqrt(cc);
+    QXD_CUDA(cudaMemcpyAsync(W.lr, W.lc, bytes, cudaMemcpyDeviceToDevice, st));
+    double rn = std::sqrt(cc);
+    int it = 0;
+    while (it < max_iter && rn > target) {
+        int k = 0;
+        for (; k < DFL_NKV && it < max_iter && rn > target; ++k, ++it) {
+            QXD_CUDA(cudaMemcpyAsync(W.lp[k], W.lr, bytes, cudaMemcpyDeviceToDevice, st));
+            if ((rc = little_apply(lat, W, W.lq[k], W.lp[k], st))) return rc;
+            if (k > 0) {
+                VecList<double2> qs{};
+                VecList<double2> ps{};
+                for (int j = 0; j < k; ++j) {
+                    qs.p[j] = W.lq[j];
+                    ps.p[j] = W.lp[j];
+                }
+                cd a[BLAS_KMAX];
+                if ((rc = blas_mdot<double2>(W.red, n, k, qs, W.lq[k], a, st))) return rc;
+                CoefList cl{};
+                for (int j = 0; j < k; ++j) {
+                    cl.re[j] = a[j].real();
+                    cl.im[j] = a[j].imag();
+                }
+                double dummy;
+                if ((rc = blas_maxpy_norm<double2>(W.red, n, k, cl, qs, W.lq[k], &dummy, st))) return rc;
+                if ((rc = blas_maxpy_norm<double2>(W.red, n, k, cl, ps, W.lp[k], &dummy, st))) return rc;
+            }
+            double qq;
+            if ((rc = blas_norm2<double2>(W.red, n, W.lq[k], &qq, st))) return rc;
+            if (!(qq > 0.0) || !std::isfinite(qq)) return fail(QXD_ERR_NUMERIC, "little solver: breakdown");
+            const double s = 1.0 / std::sqrt(qq);
+            if ((rc = blas_scale<double2>(n, s, W.lq[k], st)) || (rc = blas_scale<double2>(n, s, W.lp[k], st)))
+                return rc;
+            VecList<double2> one{};
+            one.p[0] = W.lq[k];
+            cd al;
+            if ((rc = blas_mdot<double2>(W.red, n, 1, one, W.lr, &al, st))) return rc;
+            // x += al p_k ; r -= al q_k
+            if ((rc = blas_caxpy<double2>(n, -al, W.lp[k], W.lx, st))) return rc;
+            CoefList c1{};
+            c1.re[0] = al.real();
+            c1.im[0] = al.imag();
+            double r2;
+            if ((rc = blas_maxpy_norm<double2>(W.red, n, 1, c1, one, W.lr, &r2, st))) return rc;
+            rn = std::sqrt(r2);
+        }
+    }
+    *iters = it;
+    return QXD_OK;
+}
+
+}  // namespace
+
+// out = M_dfl in = chi + SAP(in - D chi), chi = P A^-1 P^dag in (FP32 native)
+int dfl_precondition(qxd_lattice* lat, void* out, const void* in, int ncy, int nmr, double tol, int max_iter,
+                     int* little_iters, cudaStream_t st) {
+    DflWork& W = *lat->dfl;
+    const Geom& g = lat->g;
+    const size_t n32 = (size_t)12 * g.V;  // complex numbers of a field
+    int rc;
+    k_dfl_restrict<<<W.d.nblk, BSITES, 0, st>>>(g, W.d, W.ns, W.basis, (const float4*)in, W.lc);
+    QXD_LAUNCHED("k_dfl_restrict");
+    int it = 0;
+    if ((rc = little_gcr(lat, W, tol, max_iter, &it, st))) return rc;
+    if (little_iters) *little_iters += it;
+    k_dfl_prolong<<<W.d.nblk, BSITES, 0, st>>>(g, W.d, W.ns, W.basis, W.lx, W.chi);
+    QXD_LAUNCHED("k_dfl_prolong");
+    // rho = in - D chi (into W.tfield)
+    if ((rc = launch_dirac(lat, W.tfield, W.chi, QXD_FP32, st))) return rc;
+    if ((rc = blas_scale<float2>(n32, -1.0, (float2*)W.tfield, st))) return rc;
+    if ((rc = blas_caxpy<float2>(n32, cd(-1.0, 0.0), (const float2*)in, (float2*)W.tfield, st))) return rc;
+    if ((rc = sap_apply<float>(lat, W.sap, out, W.tfield, ncy, nmr, st))) return rc;
+    return blas_caxpy<float2>(n32, cd(-1.0, 0.0), (const float2*)W.chi, (float2*)out, st);
+}
+
+}  // namespace qxd
+
+using namespace qxd;
+
+namespace {
+
+int dfl_checks(qxd_lattice* lat, int ns, const char* name) {
+    if (!lat) return fail(QXD_ERR_ARG, std::string(name) + ": lat is NULL");
+    if (ns < 1 || ns > 64) return fail(QXD_ERR_ARG, std::string(name) + ": 1 <= ns <= 64");
+    if (!qxd::clover_ready(lat)) return fail(QXD_ERR_STATE, std::string(name) + ": needs qxd_sw_build first");
+    int rc = sap_check(lat);
+    if (rc) return rc;
+    if (!lat->dfl) lat->dfl = new DflWork();
+    return lat->dfl->ensure(lat->g, ns);
+}
+
+}  // namespace
+
+extern "C" {
+
+int qxd_dfl_subspace(qxd_lattice* lat, int ns, int niter, int ncy, unsigned long long seed) {
+    int rc = dfl_checks(lat, ns, "qxd_dfl_subspace");
+    if (rc) return rc;
+    if (niter < 0 || ncy < 1) return fail(QXD_ERR_ARG, "qxd_dfl_subspace: niter >= 0, ncy >= 1");
+    DflWork& W = *lat->dfl;
+    cudaStream_t st = lat->stream;
+    const size_t V = (size_t)lat->g.V;
+    W.ready = false;
+    const size_t nc = (size_t)ns * 12 * V;
+    k_dfl_random<<<4 * 152 * 4, 256, 0, st>>>(nc, seed, (float2*)W.basis);
+    QXD_LAUNCHED("k_dfl_random");
+    if ((rc = orthonormalise(lat, W, st))) return rc;
+    for (int it = 0; it < niter; ++it) {
+        for (int k = 0; k < ns; ++k) {
+            float4* v = W.basis + (size_t)k * 6 * V;
+            if ((rc = sap_apply<float>(lat, W.sap, W.tfield, v, ncy, 4, st))) return rc;
+            QXD_CUDA(cudaMemcpyAsync(v, W.tfield, 6 * V * sizeof(float4), cudaMemcpyDeviceToDevice, st));
+        }
+        if ((rc = orthonormalise(lat, W, st))) return rc;
+    }
+    return build_little(lat, W, st);
+}
+
+int qxd_dfl_set_basis(qxd_lattice* lat, int ns, const void* const* psi) {
+    int rc = dfl_checks(lat, ns, "qxd_dfl_set_basis");
+    if (rc) return rc;
+    if (!psi) return fail(QXD_ERR_ARG, "qxd_dfl_set_basis: NULL fields");
+    for (int k = 0; k < ns; ++k)
+        if (!psi[k]) return fail(QXD_ERR_ARG, "qxd_dfl_set_basis: NULL field");
+    DflWork& W = *lat->dfl;
+    cudaStream_t st = lat->stream;
+    const size_t V = (size_t)lat->g.V;
+    W.ready = false;
+    if ((rc = ensure_scratch(lat))) return rc;
+    for (int k = 0; k < ns; ++k) {
+        // lexicographic FP64 -> native FP64 (scratch) -> native FP32
+        if ((rc = launch_pack(lat, lat->scratch_in, psi[k], QXD_FP64, st))) return rc;
+        if ((rc = blas_d2f_native(V, (const double2*)lat->scratch_in, (float2*)(W.basis + (size_t)k * 6 * V), st)))
+            return rc;
+    }
+    if ((rc = orthonormalise(lat, W, st))) return rc;
+    return build_little(lat, W, st);
+}
+
+int qxd_dfl_refresh(qxd_lattice* lat) {
+    if (!lat) return fail(QXD_ERR_ARG, "qxd_dfl_refresh: lat is NULL");
+    if (!lat->dfl || !lat->dfl->basis || lat->dfl->ns == 0)
+        return fail(QXD_ERR_STATE, "qxd_dfl_refresh: no deflation subspace (qxd_dfl_subspace first)");
+    if (!qxd::clover_ready(lat)) return fail(QXD_ERR_STATE, "qxd_dfl_refresh: needs qxd_sw_build first");
+    return build_little(lat, *lat->dfl, lat->stream);
+}
+
+int qxd_dfl_little(qxd_lattice* lat, double* A_out, int* ns_out, int* nblk_out) {
+    if (!lat) return fail(QXD_ERR_ARG, "qxd_dfl_little: lat is NULL");
+    if (!lat->dfl || !lat->dfl->ready) return fail(QXD_ERR_STATE, "qxd_dfl_little: no little operator");
+    DflWork& W = *lat->dfl;
+    if (ns_out) *ns_out = W.ns;
+    if (nblk_out) *nblk_out = W.d.nblk;
+    if (!A_out) return QXD_OK;
+    const size_t n = (size_t)W.d.nblk * 9 * W.ns * W.ns;
+    std::vector<float2> h(n);
+    QXD_CUDA(cudaMemcpyAsync(h.data(), W.A, n * sizeof(float2), cudaMemcpyDeviceToHost, lat->stream));
+    QXD_CUDA(cudaStreamSynchronize(lat->stream));
+    for (size_t i = 0; i < n; ++i) {
+        A_out[2 * i] = h[i].x;
+        A_out[2 * i + 1] = h[i].y;
+    }
+    return QXD_OK;
+}
+
+int qxd_dfl_basis(qxd_lattice* lat, int k, void* out) {
+    if (!lat || !out) return fail(QXD_ERR_ARG, "qxd_dfl_basis: NULL argument");
+    if (!lat->dfl || !lat->dfl->basis || lat->dfl->ns == 0)
+        return fail(QXD_ERR_STATE, "qxd_dfl_basis: no deflation subspace");
+    if (k < 0 || k >= lat->dfl->ns) return fail(QXD_ERR_ARG, "qxd_dfl_basis: k out of range");
+    int rc;
+    if ((rc = ensure_scratch(lat))) return rc;
+    const size_t V = (size_t)lat->g.V;
+    // native FP32 -> native FP64 -> lexicographic
+    k_f32_to_f64_native<<<(unsigned)((V + 255) / 256), 256, 0, lat->stream>>>(
+        lat->g.V, lat->dfl->basis + (size_t)k * 6 * V, (double2*)lat->scratch_in);
+    QXD_LAUNCHED("k_f32_to_f64_native");
+    if ((rc = launch_unpack(lat, out, lat->scratch_in, QXD_FP64, lat->stream))) return rc;
+    QXD_CUDA(cudaStreamSynchronize(lat->stream));
+    return QXD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,45 @@
+// Local deflation work space (deflation subspace, little operator, little solver).
+#pragma once
+
+#include "blas.cuh"
+#include "qxd_internal.cuh"
+#include "solver.cuh"
+
+namespace qxd {
+
+constexpr int DFL_NKV = 16;  // Krylov vectors of the little GCR before a restart
+
+struct DflGeom {
+    int nb[4];  // blocks per direction (4^4 blocks)
+    int nblk;
+};
+
+struct DflWork {
+    int ns = 0;
+    DflGeom d{};
+    float4* basis = nullptr;   // [ns] native FP32 fields phi_k = sum_b phi_{b,k}
+    float2* A = nullptr;       // little operator [nblk][9][ns][ns]
+    float4* chi = nullptr;     // prolongation (FP32 field)
+    float4* tfield = nullptr;  // FP32 work field
+    float4* H = nullptr;       // [4] face hops (FP32 fields)
+    double2 *lx = nullptr, *lr = nullptr, *lc = nullptr;  // little vectors [nblk * ns]
+    double2* lp[DFL_NKV] = {};
+    double2* lq[DFL_NKV] = {};
+    int* d_bad = nullptr;
+    Reducer red;
+    SapWork sap;
+    unsigned op_version = 0;   // operator the little operator was built for
+    bool ready = false;
+    int ensure(const Geom& g, int ns);
+    void release();
+};
+
+void release_dfl(qxd_lattice* lat);
+// out = M_dfl in (FP32 native full-lattice fields); little_iters accumulates
+// the little-solver steps
+int dfl_precondition(qxd_lattice* lat, void* out, const void* in, int ncy, int nmr, double tol, int max_iter,
+                     int* little_iters, cudaStream_t st);
+// deflation subspace built and matching the current operator
+inline bool dfl_ready(const qxd_lattice* lat) { return lat->dfl && lat->dfl->ready && lat->dfl->op_version == lat->op_version && clover_ready(lat); }
+
+}  // namespace qxd

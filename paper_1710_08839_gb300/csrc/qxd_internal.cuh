@@ -215,6 +215,7 @@ __host__ __device__ __forceinline__ cplx<R> times_mi(cplx<R> a) { return {a.im, 
 // ---------------------------------------------------------------------------
 struct SolverWork;
 struct MscgWork;
+struct DflWork;
 }  // namespace qxd
 
 struct qxd_lattice {
@@ -252,6 +253,8 @@ struct qxd_lattice {
 
     qxd::SolverWork* solver = nullptr;  // Krylov work vectors (first solve)
     qxd::MscgWork* mscg = nullptr;      // multi-shift CG work vectors (first use)
+    qxd::DflWork* dfl = nullptr;        // deflation subspace and little operator
+    unsigned op_version = 0;            // bumped by every successful qxd_sw_build
 
     // views: a view shares the gauge field of its parent and owns its own
     // parameters, clover term, scratch and solver work
@@ -280,4 +283,5 @@ inline bool clover_ready(const qxd_lattice* lat) {
 }
 void release_solver(qxd_lattice* lat);
 void release_mscg(qxd_lattice* lat);
+void release_dfl(qxd_lattice* lat);
 }  // namespace qxd

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "blas.cuh"
+#include "dfl.cuh"
 #include "eo.cuh"
 #include "solver.cuh"
 
@@ -116,8 +117,13 @@ int apply_ain(qxd_lattice* lat, SolverWork& w, bool eo, void* out, const void* i
 
 template <typename R>
 int precondition(qxd_lattice* lat, SolverWork& w, const qxd_solver_params& P, void* out, const void* in,
-                 size_t bytes, cudaStream_t st) {
+                 size_t bytes, cudaStream_t st, qxd_solve_info& info) {
     if (P.precond == QXD_PRECOND_SAP) return sap_apply<R>(lat, w.sap, out, in, P.sap_ncy, P.sap_nmr, st);
+    if constexpr (sizeof(R) == 4) {
+        if (P.precond == QXD_PRECOND_DFL_SAP)
+            return dfl_precondition(lat, out, in, P.sap_ncy, P.sap_nmr, P.dfl_tol, P.dfl_max_iter,
+                                    &info.little_iters, st);
+    }
     QXD_CUDA(cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st));
     return QXD_OK;
 }
@@ -158,7 +164,7 @@ int fgcr(qxd_lattice* lat, SolverWork& w, const qxd_solver_params& P, double bn,
         while (k < P.nkv && info.iterations < P.max_iter) {
             V2* phk = (V2*)w.phi[k];
             V2* chk = (V2*)w.chi[k];
-            if ((rc = precondition<R>(lat, w, P, phk, rin, bytes_in, st))) return rc;
+            if ((rc = precondition<R>(lat, w, P, phk, rin, bytes_in, st, info))) return rc;
             if ((rc = apply_ain<R>(lat, w, eo, chk, phk, st))) return rc;
             ++info.inner_calls;
             // classical Gram-Schmidt against chi_0..chi_{k-1}
@@ -317,6 +323,8 @@ void qxd_solver_defaults(qxd_solver_params* p) {
     p->sap_nmr = 5;
     p->delta = 1e-4;
     p->flags = QXD_DEVICE | QXD_LAYOUT_LEX;
+    p->dfl_tol = 1e-2;
+    p->dfl_max_iter = 64;
 }
 
 int qxd_solve(qxd_lattice* lat, void* x, const void* b, const qxd_solver_params* params, qxd_solve_info* info_out,
@@ -329,20 +337,26 @@ int qxd_solve(qxd_lattice* lat, void* x, const void* b, const qxd_solver_params*
     const qxd_solver_params& P = *params;
     if (!(P.tol > 0) || P.max_iter < 1 || P.nkv < 1 || P.nkv > BLAS_KMAX)
         return fail(QXD_ERR_ARG, "qxd_solve: tol > 0, max_iter >= 1 and 1 <= nkv <= 16 required");
-    if ((P.precond != QXD_PRECOND_NONE && P.precond != QXD_PRECOND_SAP) ||
+    if ((P.precond != QXD_PRECOND_NONE && P.precond != QXD_PRECOND_SAP && P.precond != QXD_PRECOND_DFL_SAP) ||
         (P.system != QXD_SOLVE_FULL && P.system != QXD_SOLVE_EO) ||
         (P.inner_prec != QXD_FP32 && P.inner_prec != QXD_FP64) || (P.flags & ~(0x10 | 0x100)))
         return fail(QXD_ERR_ARG, "qxd_solve: bad precond/system/inner_prec/flags");
-    if (P.precond == QXD_PRECOND_SAP && P.system != QXD_SOLVE_FULL)
+    if (P.precond != QXD_PRECOND_NONE && P.system != QXD_SOLVE_FULL)
         return fail(QXD_ERR_ARG, "qxd_solve: SAP preconditions the full system only");
-    if (P.precond == QXD_PRECOND_SAP && (P.sap_ncy < 1 || P.sap_nmr < 1))
+    if (P.precond == QXD_PRECOND_DFL_SAP &&
+        (P.inner_prec != QXD_FP32 || !(P.dfl_tol > 0) || P.dfl_max_iter < 1))
+        return fail(QXD_ERR_ARG, "qxd_solve: deflation needs inner_prec FP32, dfl_tol > 0, dfl_max_iter >= 1");
+    if (P.precond != QXD_PRECOND_NONE && (P.sap_ncy < 1 || P.sap_nmr < 1))
         return fail(QXD_ERR_ARG, "qxd_solve: sap_ncy and sap_nmr must be >= 1");
     if ((P.flags & QXD_HOST) && (P.flags & QXD_LAYOUT_NATIVE))
         return fail(QXD_ERR_ARG, "qxd_solve: host buffers must use the lexicographic layout");
     if (!qxd::clover_ready(lat)) return fail(QXD_ERR_STATE, "qxd_solve: needs qxd_sw_build first");
     cudaStream_t st = stream ? (cudaStream_t)stream : lat->stream;
     int rc;
-    if (P.precond == QXD_PRECOND_SAP && (rc = sap_check(lat))) return rc;
+    if (P.precond != QXD_PRECOND_NONE && (rc = sap_check(lat))) return rc;
+    if (P.precond == QXD_PRECOND_DFL_SAP && !dfl_ready(lat))
+        return fail(QXD_ERR_STATE, "qxd_solve: no deflation subspace for the current operator "
+                                   "(qxd_dfl_subspace, or qxd_dfl_refresh after qxd_sw_build)");
     if (!lat->solver) lat->solver = new SolverWork();
     SolverWork& w = *lat->solver;
     if ((rc = w.ensure(lat->g.V, P.nkv, P.inner_prec))) return rc;

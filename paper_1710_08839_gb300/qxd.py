@@ -37,6 +37,7 @@ QXD_GAUGE_HOST = 0x10
 
 QXD_PRECOND_NONE = 0
 QXD_PRECOND_SAP = 1
+QXD_PRECOND_DFL_SAP = 2
 QXD_SOLVE_FULL = 0
 QXD_SOLVE_EO = 1
 
@@ -65,12 +66,13 @@ _d = ctypes.c_double
 
 class qxd_solver_params(ctypes.Structure):
     _fields_ = [("tol", _d), ("max_iter", _i), ("nkv", _i), ("precond", _i), ("system", _i),
-                ("inner_prec", _i), ("sap_ncy", _i), ("sap_nmr", _i), ("delta", _d), ("flags", _i)]
+                ("inner_prec", _i), ("sap_ncy", _i), ("sap_nmr", _i), ("delta", _d), ("flags", _i),
+                ("dfl_tol", _d), ("dfl_max_iter", _i)]
 
 
 class qxd_solve_info(ctypes.Structure):
     _fields_ = [("status", _i), ("iterations", _i), ("restarts", _i), ("true_relres", _d),
-                ("time_ms", _d), ("dw64_calls", _i), ("inner_calls", _i)]
+                ("time_ms", _d), ("dw64_calls", _i), ("inner_calls", _i), ("little_iters", _i)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -124,6 +126,11 @@ SIGNATURES = {
                                 ctypes.POINTER(qxd_mscg_params), ctypes.POINTER(qxd_mscg_info), _vp]),
     "qxd_gauge_observables": (_i, [_vp, _d, ctypes.POINTER(_d)]),
     "qxd_wflow": (_i, [_vp, _d, _i]),
+    "qxd_dfl_subspace": (_i, [_vp, _i, _i, _i, ctypes.c_ulonglong]),
+    "qxd_dfl_set_basis": (_i, [_vp, _i, ctypes.POINTER(_vp)]),
+    "qxd_dfl_refresh": (_i, [_vp]),
+    "qxd_dfl_little": (_i, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "qxd_dfl_basis": (_i, [_vp, _i, _vp]),
     "qxd_spinor_bytes": (ctypes.c_size_t, [_vp, _i]),
     "qxd_spinor_pack": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_spinor_unpack": (_i, [_vp, _vp, _vp, _i, _vp]),
@@ -437,6 +444,31 @@ class Lattice:
         """Wilson flow of the gauge field to t = nsteps * eps (in place);
         the clover term must be rebuilt afterwards."""
         qxd_wflow(self.handle, eps, nsteps)
+
+    def dfl_subspace(self, ns, niter=6, ncy=4, seed=1):
+        """Build the deflation subspace (ns fields) and little operator."""
+        check(_call("qxd_dfl_subspace", self.handle, ns, niter, ncy, seed))
+
+    def dfl_set_basis(self, fields):
+        """Deflation subspace from given FP64 lexicographic device fields."""
+        arr = (_vp * len(fields))(*[f.data_ptr() for f in fields])
+        check(_call("qxd_dfl_set_basis", self.handle, len(fields), arr))
+
+    def dfl_refresh(self):
+        check(_call("qxd_dfl_refresh", self.handle))
+
+    def dfl_little(self):
+        """Little operator as a complex128 numpy array (nblk, 9, ns, ns)."""
+        import numpy as np
+        ns, nblk = _i(), _i()
+        check(_call("qxd_dfl_little", self.handle, None, ctypes.byref(ns), ctypes.byref(nblk)))
+        out = np.empty(nblk.value * 9 * ns.value * ns.value * 2)
+        check(_call("qxd_dfl_little", self.handle, out.ctypes.data_as(ctypes.POINTER(_d)), None, None))
+        return out.view(np.complex128).reshape(nblk.value, 9, ns.value, ns.value)
+
+    def dfl_basis(self, k, out):
+        check(_call("qxd_dfl_basis", self.handle, k, out.data_ptr()))
+        return out
 
     def sw_logdet(self, sites=QXD_SITES_ODD) -> float:
         """sum of ln|det M(x)| over the selected sites (odd: ln|Det D_oo|)."""
