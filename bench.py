@@ -711,6 +711,49 @@ def flow_benchmark(qxd, torch):
             "flops_per_rk3_step_model": flops_step}
 
 
+# local deflation: the solver workload's lattice near its critical mass
+# (m0 = -0.62 on the eps = 0.3 field, where the SAP solver needs ~40 steps)
+DFL_WORKLOAD = dict(m0=-0.62, qhat=2, ns=16, niter=5, ncy=4, seed=3, tol=1e-10)
+
+
+def dfl_benchmark(qxd, torch):
+    """SAP-preconditioned FGCR against the deflated solver on the same
+    system; wall time of the synchronous solves, subspace build timed apart."""
+    w = SOLVE_WORKLOAD
+    D = DFL_WORKLOAD
+    su3, ang, psi, V = make_inputs("cuda", w)
+    b = psi.cuda()
+    del psi
+    lat = qxd.Lattice(w["T"], w["L1"], w["L2"], w["L3"], w["mask"])
+    lat.set_gauge(su3, ang)
+    del su3, ang
+    lat.set_params(D["m0"], w["csw"], w["cswqed"], D["qhat"])
+    lat.sw_build()
+    out = {"workload": "doubled 64x64x32x32 C* lattice, eps 0.3, csw=cswqed=1, qhat 2, m0 -0.62, tol 1e-10; "
+                       "deflation: ns 16 fields on the 4^4 SAP blocks, 5 SAP-smoothing passes"}
+    x = torch.zeros_like(b)
+    lat.solve(x, b, tol=D["tol"], precond=qxd.QXD_PRECOND_SAP, inner_prec=qxd.QXD_FP32)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, info = lat.solve(x, b, tol=D["tol"], precond=qxd.QXD_PRECOND_SAP, inner_prec=qxd.QXD_FP32)
+    out["sap"] = {"status": rc, "s": time.perf_counter() - t0, "iterations": info["iterations"],
+                  "true_relres": info["true_relres"]}
+    t0 = time.perf_counter()
+    lat.dfl_subspace(D["ns"], niter=D["niter"], ncy=D["ncy"], seed=D["seed"])
+    out["subspace_build_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lat.dfl_refresh()
+    out["little_operator_s"] = time.perf_counter() - t0
+    x2 = torch.zeros_like(b)
+    t0 = time.perf_counter()
+    rc, info = lat.solve(x2, b, tol=D["tol"], precond=qxd.QXD_PRECOND_DFL_SAP, inner_prec=qxd.QXD_FP32)
+    out["dfl_sap"] = {"status": rc, "s": time.perf_counter() - t0, "iterations": info["iterations"],
+                      "little_iters": info["little_iters"], "true_relres": info["true_relres"],
+                      "rel_diff_vs_sap": float((x2 - x).norm() / x.norm())}
+    lat.close()
+    return out
+
+
 def sap_benchmark(qxd, torch, steps, w):
     """Time one FP32 SAP application (ncy 5, nmr 5) on the lattice of workload w."""
     su3, ang, psi, V = make_inputs("cuda", w)
@@ -821,11 +864,11 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="dw", choices=["dw", "solve", "sap", "batch", "serve", "rational", "flow"],
+    ap.add_argument("--mode", default="dw", choices=["dw", "solve", "sap", "batch", "serve", "rational", "flow", "dfl"],
                     help="dw: the Dw throughput line (plus a solver summary unless --no-solve); "
                          "solve: solver comparison only; sap: time the SAP preconditioner only; "
                          "batch / serve: multi-RHS and serving workloads; rational: pseudofermion action; "
-                         "flow: Wilson flow and gauge observables")
+                         "flow: Wilson flow and gauge observables; dfl: deflated vs SAP solver")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--write-traffic", metavar="NCU_CSV",
                     help="write profiles/dirac_fp32_q2_traffic.json from an ncu CSV of k_dirac launches and exit")
@@ -849,8 +892,10 @@ def main():
     ge.build()
     from paper_1710_08839_gb300 import qxd
 
-    if args.mode in ("solve", "sap", "batch", "serve", "rational", "flow"):
-        if args.mode == "flow":
+    if args.mode in ("solve", "sap", "batch", "serve", "rational", "flow", "dfl"):
+        if args.mode == "dfl":
+            res = dfl_benchmark(qxd, torch)
+        elif args.mode == "flow":
             res = flow_benchmark(qxd, torch)
         elif args.mode == "solve":
             res = solve_benchmark(qxd, torch)
