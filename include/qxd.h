@@ -348,8 +348,14 @@ int qxd_sw_logdet(qxd_lattice* lat, int sites, double* out);
 
 typedef struct {
     double tol;       /* stop when each shift's residual is <= tol |b|             */
-    int max_iter;     /* limit on CG steps                                        */
+    int max_iter;     /* limit on CG steps (all passes together)                   */
     int flags;        /* x and b: QXD_DEVICE | QXD_HOST, QXD_LAYOUT_LEX | _NATIVE  */
+    int prec;         /* QXD_FP64: FP64 throughout. QXD_FP32: the operator in FP32 */
+                      /* (vectors and scalars FP64), the base residual replaced by */
+                      /* the true FP64 residual whenever it fell by delta, then    */
+                      /* each shift checked in FP64 and refined by FP32-operator   */
+                      /* CG on its residual until it meets tol                     */
+    double delta;     /* QXD_FP32: reliable-update factor, 0 < delta < 1           */
 } qxd_mscg_params;
 
 typedef struct {
@@ -361,7 +367,8 @@ typedef struct {
     int dhat_calls;         /* applications of D_hat (A costs two)                  */
 } qxd_mscg_info;
 
-/* Defaults: tol 1e-10, max_iter 10000, device lexicographic buffers. */
+/* Defaults: tol 1e-10, max_iter 10000, device lexicographic buffers, FP64,
+ * delta 0.01. */
 void qxd_mscg_defaults(qxd_mscg_params* p);
 
 /*

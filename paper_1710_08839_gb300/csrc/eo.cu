@@ -146,6 +146,7 @@ int apply_g5dhat(qxd_lattice* lat, SpRefOut<R> out_e, SpRef<R> in_e, SpRefOut<R>
     if (rc) return rc;
     return launch_eo<R>(lat, EO_G5_CLOVER_AUX_MHOP, 0, as_in(tmp_o), in_e, out_e, false, st);
 }
+template int apply_g5dhat<float>(qxd_lattice*, SpRefOut<float>, SpRef<float>, SpRefOut<float>, cudaStream_t);
 template int apply_g5dhat<double>(qxd_lattice*, SpRefOut<double>, SpRef<double>, SpRefOut<double>, cudaStream_t);
 
 namespace {

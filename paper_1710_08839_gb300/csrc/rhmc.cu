@@ -180,6 +180,61 @@ __global__ void __launch_bounds__(RED_THREADS) k_ms_true_res(size_t n, double si
     block_reduce_store<1>(acc, 1, partials);
 }
 
+// FP32 native half-lattice layout: component k of site s at float2 index
+// ((k / 2) * S + s) * 2 + k % 2 (two components per float4)
+__device__ __forceinline__ size_t f32_half_index(size_t S, size_t i) {
+    const size_t k = i / S, s = i - k * S;
+    return ((k >> 1) * S + s) * 2 + (k & 1);
+}
+
+// r -= alpha (w32 + sigma0 p), w32 in the FP32 native layout; returns |r|^2
+__global__ void __launch_bounds__(RED_THREADS) k_ms_residual32(size_t n, size_t S, double alpha, double sigma0,
+                                                              const float2* __restrict__ w,
+                                                              const double2* __restrict__ p,
+                                                              double2* __restrict__ r,
+                                                              double* __restrict__ partials) {
+    double acc[1] = {0.0};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 a = w[f32_half_index(S, i)];
+        const double2 b = p[i];
+        double2 v = r[i];
+        v.x -= alpha * ((double)a.x + sigma0 * b.x);
+        v.y -= alpha * ((double)a.y + sigma0 * b.y);
+        r[i] = v;
+        acc[0] += v.x * v.x + v.y * v.y;
+    }
+    block_reduce_store<1>(acc, 1, partials);
+}
+
+// r = b - w - sigma x (FP64), returns |r|^2
+__global__ void __launch_bounds__(RED_THREADS) k_ms_true_res_store(size_t n, double sigma,
+                                                                  const double2* __restrict__ b,
+                                                                  const double2* __restrict__ w,
+                                                                  const double2* __restrict__ x,
+                                                                  double2* __restrict__ r,
+                                                                  double* __restrict__ partials) {
+    double acc[1] = {0.0};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 bv = b[i], wv = w[i], xv = x[i];
+        const double re = bv.x - wv.x - sigma * xv.x;
+        const double im = bv.y - wv.y - sigma * xv.y;
+        r[i] = make_double2(re, im);
+        acc[0] += re * re + im * im;
+    }
+    block_reduce_store<1>(acc, 1, partials);
+}
+
+// x += a p (FP64)
+__global__ void k_ms_axpy(size_t n, double a, const double2* __restrict__ p, double2* __restrict__ x) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double2 v = x[i];
+        const double2 q = p[i];
+        v.x += a * q.x;
+        v.y += a * q.y;
+        x[i] = v;
+    }
+}
+
 struct Combine {
     int k;
     double rho[BLAS_KMAX];
@@ -234,7 +289,13 @@ int dev_alloc(double2** p, size_t bytes) {
 }  // namespace
 
 void MscgWork::release() {
-    double2** ps[] = {&b, &r, &t, &w, &tmp_o, &full, &out};
+    double2** ps[] = {&b, &r, &t, &w, &tmp_o, &full, &out, &e, &src2};
+    float4** fs[] = {&p32, &t32, &w32, &tmp32};
+    for (float4** p : fs)
+        if (*p) {
+            cudaFree(*p);
+            *p = nullptr;
+        }
     for (double2** p : ps)
         if (*p) {
             cudaFree(*p);
@@ -256,9 +317,12 @@ int MscgWork::ensure(int V_, int Vh_, int nshift_) {
     int rc;
     if (Vh != Vh_) {
         release();
-        double2** ps[] = {&b, &r, &t, &w, &tmp_o, &out};
+        double2** ps[] = {&b, &r, &t, &w, &tmp_o, &out, &e, &src2};
         for (double2** p : ps)
             if ((rc = dev_alloc(p, hb))) return rc;
+        float4** fs[] = {&p32, &t32, &w32, &tmp32};
+        for (float4** p : fs)
+            if ((rc = dev_alloc((double2**)p, hb / 2))) return rc;
         if ((rc = dev_alloc(&full, (size_t)12 * V_ * sizeof(double2)))) return rc;
         if ((rc = red.init())) return rc;
         Vh = Vh_;
@@ -416,9 +480,201 @@ int mscg_core(qxd_lattice* lat, MscgWork& W, int ns, const double* sigma, double
 
 namespace {
 
+// Q32 in = gamma5 D_hat in with the FP32 operator (even-site FP32 arrays)
+int apply_q32(qxd_lattice* lat, MscgWork& W, float4* out, const float4* in, cudaStream_t st) {
+    const int Vh = lat->g.Vh;
+    return apply_g5dhat<float>(lat, half_out<float>(out, Vh, 0), half_ref<float>(in, Vh, 0),
+                               half_out<float>(W.tmp32, Vh, 1), st);
+}
+
+// Multi-shift CG with the FP32 operator: the Krylov vectors, x_j and all
+// scalars are FP64; the base residual is replaced by the true FP64 residual
+// src - (A + s0) x_base whenever it has fallen by delta since the last
+// replacement, and before the run ends. Solves (A + sigma_j) x_j = src into
+// x[j] until every shift's iterated residual is below target (absolute).
+// *true_rr: |src - (A + s0) x_base|^2 from the last reliable update when the
+// run ended converged (that update is the last step), else -1.
+int run_mixed(qxd_lattice* lat, MscgWork& W, const double2* src, double ss, int ns, const double* sigma,
+              double2* const* x, double target, double delta, int max_iter, int* iters, double* true_rr,
+              qxd_mscg_info& info, cudaStream_t st) {
+    const size_t Vh = (size_t)lat->g.Vh;
+    const size_t n = 12 * Vh;
+    const size_t hb = n * sizeof(double2);
+    int base = 0;
+    for (int j = 1; j < ns; ++j)
+        if (sigma[j] < sigma[base]) base = j;
+    const double s0 = sigma[base];
+    int rc;
+    for (int j = 0; j < ns; ++j) QXD_CUDA(cudaMemsetAsync(x[j], 0, hb, st));
+    *iters = 0;
+    *true_rr = -1.0;
+    if (ss == 0.0) {
+        *true_rr = 0.0;
+        return QXD_OK;
+    }
+    QXD_CUDA(cudaMemcpyAsync(W.r, src, hb, cudaMemcpyDeviceToDevice, st));
+    for (int j = 0; j < ns; ++j) QXD_CUDA(cudaMemcpyAsync(W.p[j], src, hb, cudaMemcpyDeviceToDevice, st));
+    std::vector<double> zeta(ns, 1.0), zeta_prev(ns, 1.0), zeta_new(ns, 1.0);
+    std::vector<char> active(ns, 1);
+    double rr = ss, pp = ss, alpha_prev = 1.0, beta_prev = 0.0, rr_max = ss;
+    int it = 0;
+    const unsigned ew = (unsigned)std::min<size_t>((n + 255) / 256, 4 * 152 * 4);
+    while (it < max_iter) {
+        if ((rc = blas_d2f_native(Vh, W.p[base], (float2*)W.p32, st))) return rc;
+        if ((rc = apply_q32(lat, W, W.t32, W.p32, st)) || (rc = apply_q32(lat, W, W.w32, W.t32, st))) return rc;
+        info.dhat_calls += 2;
+        double tt;
+        if ((rc = blas_norm2<float2>(W.red, n, (const float2*)W.t32, &tt, st))) return rc;
+        const double alpha = rr / (tt + s0 * pp);
+        if (!std::isfinite(alpha) || !(alpha > 0.0))
+            return fail(QXD_ERR_NUMERIC, "qxd_mscg: breakdown (non-finite or non-positive step)");
+        double rr_new;
+        if ((rc = reduce_launch(W, k_ms_residual32, 1, &rr_new, st, n, Vh, alpha, s0, (const float2*)W.w32,
+                                (const double2*)W.p[base], W.r)))
+            return rc;
+        // reliable update of the base residual
+        const bool base_done = std::sqrt(rr_new) <= target;
+        const bool reliable = rr_new < delta * delta * rr_max || base_done;
+        if (reliable) {
+            k_ms_axpy<<<ew, 256, 0, st>>>(n, alpha, W.p[base], x[base]);
+            QXD_LAUNCHED("k_ms_axpy");
+            if ((rc = apply_normal(lat, W, x[base], st))) return rc;
+            info.dhat_calls += 2;
+            if ((rc = reduce_launch(W, k_ms_true_res_store, 1, &rr_new, st, n, s0, src, (const double2*)W.w,
+                                    (const double2*)x[base], W.r)))
+                return rc;
+            rr_max = rr_new;
+        }
+        const double beta = rr_new / rr;
+        ShiftUpdate u{};
+        u.base = -1;
+        for (int j = 0; j < ns; ++j) {
+            if (!active[j]) continue;
+            double a, z, b;
+            if (j == base) {
+                a = reliable ? 0.0 : alpha;  // already added on a reliable update
+                z = 1.0;
+                b = beta;
+                zeta_new[j] = 1.0;
+                u.base = u.k;
+            } else {
+                const double ds = sigma[j] - s0;
+                const double den = alpha_prev * zeta_prev[j] * (1.0 + alpha * ds) +
+                                   alpha * beta_prev * (zeta_prev[j] - zeta[j]);
+                zeta_new[j] = zeta[j] * zeta_prev[j] * alpha_prev / den;
+                const double q = zeta_new[j] / zeta[j];
+                a = alpha * q;
+                z = zeta_new[j];
+                b = beta * q * q;
+            }
+            u.a[u.k] = a;
+            u.z[u.k] = z;
+            u.b[u.k] = b;
+            u.x[u.k] = x[j];
+            u.p[u.k] = W.p[j];
+            ++u.k;
+        }
+        double pp_new = 0.0;
+        if ((rc = reduce_launch(W, k_ms_xp, 1, &pp_new, st, n, u, (const double2*)W.r))) return rc;
+        ++it;
+        for (int j = 0; j < ns; ++j) {
+            if (!active[j]) continue;
+            zeta_prev[j] = zeta[j];
+            zeta[j] = zeta_new[j];
+            if (j != base && std::fabs(zeta[j]) * std::sqrt(rr_new) <= target) active[j] = 0;
+        }
+        alpha_prev = alpha;
+        beta_prev = beta;
+        rr = rr_new;
+        pp = pp_new;
+        if (reliable && std::sqrt(rr) <= target) {  // the true base residual (just replaced)
+            *true_rr = rr;
+            break;
+        }
+    }
+    *iters = it;
+    return QXD_OK;
+}
+
+// FP32-operator multi-shift CG, then every shift checked in FP64 and
+// refined by FP32-operator CG on its own residual until it meets tol
+int mscg_mixed(qxd_lattice* lat, MscgWork& W, int ns, const double* sigma, double tol, double delta,
+               int max_iter, qxd_mscg_info& info, double* relres, cudaStream_t st) {
+    const size_t n = (size_t)12 * lat->g.Vh;
+    const unsigned ew = (unsigned)std::min<size_t>((n + 255) / 256, 4 * 152 * 4);
+    int rc;
+    double bb;
+    if ((rc = blas_norm2<double2>(W.red, n, W.b, &bb, st))) return rc;
+    if (relres)
+        for (int j = 0; j < ns; ++j) relres[j] = 0.0;
+    info.true_relres = 0.0;
+    if (bb == 0.0) {
+        for (int j = 0; j < ns; ++j) QXD_CUDA(cudaMemsetAsync(W.x[j], 0, n * sizeof(double2), st));
+        return QXD_OK;
+    }
+    if (!std::isfinite(bb)) return fail(QXD_ERR_NUMERIC, "qxd_mscg: non-finite source");
+    const double bn = std::sqrt(bb);
+    int it = 0;
+    double rr_fin;
+    if ((rc = run_mixed(lat, W, W.b, bb, ns, sigma, W.x, tol * bn, delta, max_iter, &it, &rr_fin, info, st)))
+        return rc;
+    int total = it;
+    double worst = 0.0;
+    bool ok = true;
+    for (int j = 0; j < ns; ++j) {
+        double rel = 0.0;
+        double r2 = -1.0;  // true |b - (A + sigma_j) x_j|^2 when known
+        for (int pass = 0;; ++pass) {
+            if (r2 < 0.0) {
+                if ((rc = apply_normal(lat, W, W.x[j], st))) return rc;
+                info.dhat_calls += 2;
+                if ((rc = reduce_launch(W, k_ms_true_res_store, 1, &r2, st, n, sigma[j], (const double2*)W.b,
+                                        (const double2*)W.w, (const double2*)W.x[j], W.src2)))
+                    return rc;
+            }
+            rel = std::sqrt(r2) / bn;
+            if (!std::isfinite(rel)) return fail(QXD_ERR_NUMERIC, "qxd_mscg: non-finite true residual");
+            if (rel <= tol || pass == 4 || total >= max_iter) break;
+            // x_j += e, (A + sigma_j) e = r_j to half the target; the refinement
+            // ends with the true residual of its system, which is the new
+            // residual r_j - (A + sigma_j) e of x_j
+            double2* xe[1] = {W.e};
+            int it2 = 0;
+            double rr_e;
+            if ((rc = run_mixed(lat, W, W.src2, r2, 1, &sigma[j], xe, 0.5 * tol * bn, delta, max_iter - total,
+                                &it2, &rr_e, info, st)))
+                return rc;
+            total += it2;
+            k_ms_axpy<<<ew, 256, 0, st>>>(n, 1.0, W.e, W.x[j]);
+            QXD_LAUNCHED("k_ms_axpy");
+            r2 = rr_e;  // -1 (recompute) unless the refinement converged
+        }
+        if (relres) relres[j] = rel;
+        worst = std::max(worst, rel);
+        if (rel > tol) ok = false;
+    }
+    info.iterations = total;
+    info.true_relres = worst;
+    if (!ok)
+        return fail(QXD_ERR_NOT_CONVERGED, "qxd_mscg: largest true relative residual " + std::to_string(worst) +
+                                               " (tol " + std::to_string(tol) + ") after " + std::to_string(total) +
+                                               " steps");
+    return QXD_OK;
+}
+
+int solve_shifts(qxd_lattice* lat, MscgWork& W, int ns, const double* sigma, const qxd_mscg_params& P,
+                 qxd_mscg_info& info, double* relres, cudaStream_t st) {
+    if (P.prec == QXD_FP32) return mscg_mixed(lat, W, ns, sigma, P.tol, P.delta, P.max_iter, info, relres, st);
+    return mscg_core(lat, W, ns, sigma, P.tol, P.max_iter, info, relres, st);
+}
+
 int check_params(const qxd_mscg_params* P, const char* name) {
     if (!P) return fail(QXD_ERR_ARG, std::string(name) + ": NULL params");
     if (!(P->tol > 0) || P->max_iter < 1) return fail(QXD_ERR_ARG, std::string(name) + ": tol > 0, max_iter >= 1");
+    if (P->prec != QXD_FP64 && P->prec != QXD_FP32)
+        return fail(QXD_ERR_ARG, std::string(name) + ": prec must be QXD_FP64 or QXD_FP32");
+    if (P->prec == QXD_FP32 && !(P->delta > 0.0 && P->delta < 1.0))
+        return fail(QXD_ERR_ARG, std::string(name) + ": 0 < delta < 1 required with QXD_FP32");
     if (P->flags & ~(QXD_HOST | QXD_LAYOUT_NATIVE))
         return fail(QXD_ERR_ARG, std::string(name) + ": flags: QXD_HOST, QXD_LAYOUT_NATIVE only (FP64 fields)");
     if ((P->flags & QXD_HOST) && (P->flags & QXD_LAYOUT_NATIVE))
@@ -513,6 +769,8 @@ void qxd_mscg_defaults(qxd_mscg_params* p) {
     p->tol = 1e-10;
     p->max_iter = 10000;
     p->flags = QXD_DEVICE | QXD_LAYOUT_LEX;
+    p->prec = QXD_FP64;
+    p->delta = 0.01;
 }
 
 int qxd_mscg(qxd_lattice* lat, int nshift, const double* sigma, void* const* x, const void* b,
@@ -534,7 +792,7 @@ int qxd_mscg(qxd_lattice* lat, int nshift, const double* sigma, void* const* x, 
     cudaStream_t st = stream ? (cudaStream_t)stream : lat->stream;
     MscgWork& W = *lat->mscg;
     if ((rc = load_source(lat, W, b, params->flags, st))) return rc;
-    rc = mscg_core(lat, W, nshift, sigma, params->tol, params->max_iter, info, relres, st);
+    rc = solve_shifts(lat, W, nshift, sigma, *params, info, relres, st);
     if (rc == QXD_OK || rc == QXD_ERR_NOT_CONVERGED) {
         int rc2 = QXD_OK;
         for (int j = 0; j < nshift && !rc2; ++j) rc2 = store_field(lat, W, x[j], W.x[j], params->flags, st);
@@ -577,7 +835,7 @@ int qxd_rational_apply(qxd_lattice* lat, int n, const double* nu, const double* 
     cudaStream_t st = stream ? (cudaStream_t)stream : lat->stream;
     MscgWork& W = *lat->mscg;
     if ((rc = load_source(lat, W, phi, params->flags, st))) return rc;
-    rc = mscg_core(lat, W, n, s.data(), params->tol, params->max_iter, info, nullptr, st);
+    rc = solve_shifts(lat, W, n, s.data(), *params, info, nullptr, st);
     if (rc == QXD_OK || rc == QXD_ERR_NOT_CONVERGED) {
         Combine c{};
         c.k = n;

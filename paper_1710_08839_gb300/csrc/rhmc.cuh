@@ -12,6 +12,8 @@ struct MscgWork {
     // even-site FP64 arrays (12 V/2 complex numbers each)
     double2 *b = nullptr, *r = nullptr, *t = nullptr, *w = nullptr, *out = nullptr;
     double2* tmp_o = nullptr;  // odd-site temporary of D_hat
+    double2 *e = nullptr, *src2 = nullptr;  // refinement: correction and residual
+    float4 *p32 = nullptr, *t32 = nullptr, *w32 = nullptr, *tmp32 = nullptr;  // FP32 operator (even/odd sites)
     double2* full = nullptr;   // full-lattice native FP64 staging field
     double2* x[BLAS_KMAX] = {};
     double2* p[BLAS_KMAX] = {};

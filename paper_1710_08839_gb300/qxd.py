@@ -79,7 +79,7 @@ class qxd_solve_info(ctypes.Structure):
 
 
 class qxd_mscg_params(ctypes.Structure):
-    _fields_ = [("tol", _d), ("max_iter", _i), ("flags", _i)]
+    _fields_ = [("tol", _d), ("max_iter", _i), ("flags", _i), ("prec", _i), ("delta", _d)]
 
 
 class qxd_mscg_info(ctypes.Structure):

@@ -67,7 +67,7 @@ def test_pseudofermion_entry_points_check_arguments():
     out = ctypes.c_double()
     assert lib.qxd_sw_logdet(None, qxd.QXD_SITES_ODD, ctypes.byref(out)) == qxd.QXD_ERR_ARG
     p = qxd.qxd_mscg_defaults()
-    assert (p.tol, p.max_iter, p.flags) == (1e-10, 10000, 0)
+    assert (p.tol, p.max_iter, p.flags, p.prec, p.delta) == (1e-10, 10000, 0, 0, 0.01)
     info = qxd.qxd_mscg_info()
     sig = (ctypes.c_double * 1)(0.1)
     xs = (ctypes.c_void_p * 1)(None)

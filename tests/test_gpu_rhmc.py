@@ -190,3 +190,42 @@ def test_rational_apply_full_size_properties(qxd):
     res = _g5(w.reshape(V, 4, 3)) + s * x[0].reshape(V, 4, 3) - pe
     res[~even] = 0
     assert (res.norm() / pe.norm()).item() <= 1e-9
+
+
+@pytest.mark.parametrize("name", ["cstar_q2", "periodic_q0"])
+def test_mixed_precision_mscg_matches_oracle(qxd, name):
+    """FP32 operator with FP64 reliable updates and per-shift refinement:
+    the same solutions (to the cond * tol bound) and true residuals <= tol."""
+    c = Case(**CASES[name])
+    eo = O.EvenOdd(c.oracle())
+    lat = c.lattice()
+    sig = [0.3, 0.04, 2.5, 1.0]
+    b = c.psi.to(torch.complex128).cuda().contiguous()
+    xs = [torch.empty_like(b) for _ in sig]
+    rc, info, rel = lat.mscg(xs, b, sig, tol=1e-12, prec=qxd.QXD_FP32)
+    assert rc == qxd.QXD_OK, info
+    assert max(rel) <= 1e-12
+    be = c.psi.numpy()[eo.even]
+    for s, x in zip(sig, xs):
+        xh = x.cpu().numpy()
+        assert np.all(xh[eo.odd] == 0)
+        ref, _, _ = O.shifted_solve(eo, be, s, tol=1e-13)
+        assert rel_norm(xh[eo.even], ref) < 1e-8, s
+
+
+def test_mixed_precision_rational_apply(qxd):
+    c = Case(**CASES["cstar_qm1_ragged"])
+    eo = O.EvenOdd(c.oracle())
+    lat = c.lattice()
+    nu, mu = PR.factor_P(1)
+    phi = c.psi.to(torch.complex128).cuda().contiguous()
+    out = torch.empty_like(phi)
+    rc, info = lat.rational_apply(out, phi, nu, mu, tol=1e-12, prec=qxd.QXD_FP32)
+    assert rc == qxd.QXD_OK and info["true_relres"] <= 1e-12, info
+    pe = c.psi.numpy()[eo.even]
+    ref = O.rational_apply(eo, pe, nu, mu)
+    assert rel_norm(out.cpu().numpy()[eo.even], ref) < 1e-9
+    # a bad delta is an argument error
+    with pytest.raises(qxd.QxdError) as e:
+        lat.rational_apply(out, phi, nu, mu, prec=qxd.QXD_FP32, delta=1.5)
+    assert e.value.code == qxd.QXD_ERR_ARG
