@@ -24,10 +24,13 @@ int cuda_fail(cudaError_t e, const char* what) {
 }
 
 static int pick_sweep_rows(int N1, int N2, int N3) {
-    // largest divisor R of N2 with N1 * R * N3 <= 48K sites
+    // largest divisor R of N2 with N1 * R * N3 <= 64K sites: the x0 neighbours
+    // of a site are that many sites apart in the sweep, and their data must
+    // still be in L2 (measured on the 96x96x48x48 lattice: 24K-site windows
+    // and whole x2 extents are slower, 55K-74K best)
     int best = 1;
     for (int R = 1; R <= N2; ++R)
-        if (N2 % R == 0 && (long long)N1 * R * N3 <= 49152) best = R;
+        if (N2 % R == 0 && (long long)N1 * R * N3 <= 65536) best = R;
     return best;
 }
 

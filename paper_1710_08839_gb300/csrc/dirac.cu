@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(DW_THREADS, DwMinBlocks<R>::value) k_dirac(Geo
     clover_mul(f.C, g.V, s, v, w);
 #pragma unroll
     for (int i = 0; i < 12; ++i) w[i] = w[i] - R(0.5) * acc[i];
-    store_spinor(f.out, g.V, s, w);
+    if constexpr (sizeof(R) == 4) store_spinor_cs(f.out, g.V, s, w);
+    else store_spinor(f.out, g.V, s, w);
 }
 
 // lexicographic [site][spin][colour][re,im] <-> native structure of arrays

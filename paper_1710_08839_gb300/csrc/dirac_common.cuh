@@ -65,6 +65,12 @@ __device__ __forceinline__ void store_spinor(float4* __restrict__ p, int V, int 
 #pragma unroll
     for (int k = 0; k < 6; ++k) p[(size_t)k * V + s] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
 }
+// streaming (evict-first) store, for outputs not read again by the kernel
+__device__ __forceinline__ void store_spinor_cs(float4* __restrict__ p, int V, int s, const cplx<float> v[12]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        __stcs(&p[(size_t)k * V + s], make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im));
+}
 __device__ __forceinline__ void store_spinor(double2* __restrict__ p, int V, int s, const cplx<double> v[12]) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) p[(size_t)k * V + s] = make_double2(v[k].re, v[k].im);
@@ -206,7 +212,8 @@ __device__ __forceinline__ void clover_mul(const float4* __restrict__ C, int V, 
         float r[36];
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            float4 t = C[(size_t)(9 * blk + q) * V + s];
+            // the clover term is read once per kernel: streaming (evict-first) load
+            float4 t = __ldcs(&C[(size_t)(9 * blk + q) * V + s]);
             r[4 * q] = t.x;
             r[4 * q + 1] = t.y;
             r[4 * q + 2] = t.z;

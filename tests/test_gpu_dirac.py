@@ -62,16 +62,20 @@ def test_dirac_parity(name):
 
 
 def test_multi_chunk_sweep_sampled():
-    """A lattice whose sweep has several x2 chunks (N1*N2*N3 > 48K): FP64 and
-    FP32 against the oracle on 3000 sampled sites."""
+    """A lattice whose sweep has several x2 chunks (N1*N2*N3 > 64K sites, so
+    the x2 extent is cut into chunks): FP64 and FP32 against the oracle on 3000
+    sampled sites plus every site of the rows next to the chunk boundary."""
     from paper_1710_08839_gb300 import qxd
-    c = Case(T=4, L1=8, L2=64, L3=64, qhat=2)
+    c = Case(T=4, L1=8, L2=128, L3=64, qhat=2)
     lat = c.lattice()
     y64 = gpu_apply(lat, c.psi, qxd.QXD_FP64)
     y32 = gpu_apply(lat, c.psi, qxd.QXD_FP32)
     lat.close()
     rng = np.random.default_rng(0)
-    idx = rng.choice(c.V, size=3000, replace=False)
+    olat = O.Lattice(c.T, c.L1, c.L2, c.L3, c.mask)
+    x2 = olat.coords(olat.all_sites())[:, 2]
+    rows = np.nonzero(np.isin(x2, (0, 63, 64, 127)))[0]
+    idx = np.union1d(rng.choice(c.V, size=3000, replace=False), rows[::7])
     ref = c.oracle().apply_at(c.psi.numpy(), idx)
     assert rel_max(y64[idx], ref) < TOL64
     assert rel_norm(y32[idx], ref) < TOL32
