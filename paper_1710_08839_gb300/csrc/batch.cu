@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(DW_THREADS, DwMinBlocks<R>::value)
     dirac_dir<R, true, 3>(g, f, psi, g.V, 0, q, x0, x1, x2, x3, s, po, acc);
     cplx<R> v[12], w[12];
     load_spinor(psi, g.V, s, v);
-    clover_mul(f.C, g.V, s, v, w);
+    clover_mul<true>(f.C, g.V, s, v, w);
 #pragma unroll
     for (int i = 0; i < 12; ++i) w[i] = w[i] - R(0.5) * acc[i];
     store_spinor(G.out[r], g.V, s, w);

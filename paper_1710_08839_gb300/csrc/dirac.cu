@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(DW_THREADS, DwMinBlocks<R>::value) k_dirac(Geo
     dirac_dir<R, QNZ, 3>(g, f, f.psi, g.V, 0, q, x0, x1, x2, x3, s, po, acc);
     cplx<R> v[12], w[12];
     load_spinor(f.psi, g.V, s, v);
-    clover_mul(f.C, g.V, s, v, w);
+    clover_mul<true>(f.C, g.V, s, v, w);
 #pragma unroll
     for (int i = 0; i < 12; ++i) w[i] = w[i] - R(0.5) * acc[i];
     if constexpr (sizeof(R) == 4) store_spinor_cs(f.out, g.V, s, w);

@@ -8,14 +8,15 @@
 
 namespace qxd {
 
-constexpr int DW_THREADS = 256;
+constexpr int DW_THREADS = 128;
 
-// Register budget of the stencil kernels: FP32 at most 80 registers (3 blocks
-// of 256 threads per SM); the kernels are latency bound and more resident
-// warps keep more loads in flight. FP64 at most 128 (2 blocks).
+// Register budget of the stencil kernels: FP32 at most 80 registers (6 blocks
+// of 128 threads per SM); the kernels are latency bound and more resident
+// warps keep more loads in flight. FP64 at most 128 (4 blocks). Blocks of
+// 128 threads measured faster than 256 or 64 at the same budget.
 template <typename R>
 struct DwMinBlocks {
-    static constexpr int value = sizeof(R) == 4 ? 3 : 2;
+    static constexpr int value = sizeof(R) == 4 ? 6 : 4;
 };
 
 template <typename R>
@@ -205,6 +206,9 @@ __device__ __forceinline__ void herm6_mul(const R d[6], const cplx<R> L[15], con
         }
 }
 
+// STREAM: evict-first loads, for kernels that read each clover block once per
+// launch (not the Schwarz block solves, which re-read it every MR step)
+template <bool STREAM = false>
 __device__ __forceinline__ void clover_mul(const float4* __restrict__ C, int V, int s, const cplx<float> v[12],
                                            cplx<float> w[12]) {
 #pragma unroll
@@ -212,8 +216,7 @@ __device__ __forceinline__ void clover_mul(const float4* __restrict__ C, int V, 
         float r[36];
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            // the clover term is read once per kernel: streaming (evict-first) load
-            float4 t = __ldcs(&C[(size_t)(9 * blk + q) * V + s]);
+            float4 t = STREAM ? __ldcs(&C[(size_t)(9 * blk + q) * V + s]) : C[(size_t)(9 * blk + q) * V + s];
             r[4 * q] = t.x;
             r[4 * q + 1] = t.y;
             r[4 * q + 2] = t.z;
@@ -229,6 +232,7 @@ __device__ __forceinline__ void clover_mul(const float4* __restrict__ C, int V, 
     }
 }
 
+template <bool STREAM = false>
 __device__ __forceinline__ void clover_mul(const double* __restrict__ C, int V, int s, const cplx<double> v[12],
                                            cplx<double> w[12]) {
 #pragma unroll

@@ -48,11 +48,11 @@ __global__ void __launch_bounds__(DW_THREADS, DwMinBlocksEo<R>::value)
         cplx<R> t[12];
 #pragma unroll
         for (int i = 0; i < 12; ++i) t[i] = R(-0.5) * acc[i];
-        clover_mul(Cl, g.V, s, t, w);
+        clover_mul<true>(Cl, g.V, s, t, w);
     } else if (MODE == EO_CLOVER_AUX_MHOP || MODE == EO_G5_CLOVER_AUX_MHOP) {
         cplx<R> a[12];
         load_spinor(aux.p, aux.stride, s - aux.off, a);
-        clover_mul(Cl, g.V, s, a, w);
+        clover_mul<true>(Cl, g.V, s, a, w);
 #pragma unroll
         for (int i = 0; i < 12; ++i) w[i] = w[i] + R(0.5) * acc[i];
         if (MODE == EO_G5_CLOVER_AUX_MHOP) {
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(DW_THREADS, DwMinBlocksEo<R>::value)
         load_spinor(aux.p, aux.stride, s - aux.off, a);
 #pragma unroll
         for (int i = 0; i < 12; ++i) a[i] = a[i] + R(0.5) * acc[i];
-        clover_mul(Cl, g.V, s, a, w);
+        clover_mul<true>(Cl, g.V, s, a, w);
     }
     store_spinor(out.p, out.stride, s - out.off, w);
 }
@@ -83,7 +83,7 @@ __global__ void k_clover_half(Geom g, int p, SpRef<R> in, SpRefOut<R> out,
     const int s = p * g.Vh + h;
     cplx<R> a[12], w[12];
     load_spinor(in.p, in.stride, s - in.off, a);
-    clover_mul(Cl, g.V, s, a, w);
+    clover_mul<true>(Cl, g.V, s, a, w);
     store_spinor(out.p, out.stride, s - out.off, w);
 }
 
