@@ -315,17 +315,28 @@ int qxd_Dw(qxd_lattice* lat, void* out, const void* in, int flags, void* stream)
     size_t bytes = qxd_spinor_bytes(lat, prec);
     const void* lex_in = in;
     if (host) {
-        QXD_CUDA(cudaMemcpyAsync(lat->scratch_lex, in, bytes, cudaMemcpyHostToDevice, st));
-        lex_in = lat->scratch_lex;
-    }
-    if ((rc = launch_pack(lat, lat->scratch_in, lex_in, prec, st))) return rc;
-    if ((rc = launch_dirac(lat, lat->scratch_out, lat->scratch_in, prec, st))) return rc;
-    if (host) {
-        if ((rc = launch_unpack(lat, lat->scratch_lex, lat->scratch_out, prec, st))) return rc;
-        QXD_CUDA(cudaMemcpyAsync(out, lat->scratch_lex, bytes, cudaMemcpyDeviceToHost, st));
+        // page-locked buffers are read and written by the kernels directly;
+        // pageable ones go through a device staging copy
+        void* in_dev = nullptr;
+        void* out_dev = nullptr;
+        if (host_device_view(in, &in_dev)) {
+            if ((rc = launch_pack_from_host(lat, lat->scratch_in, in_dev, prec, st))) return rc;
+        } else {
+            QXD_CUDA(cudaMemcpyAsync(lat->scratch_lex, in, bytes, cudaMemcpyHostToDevice, st));
+            if ((rc = launch_pack(lat, lat->scratch_in, lat->scratch_lex, prec, st))) return rc;
+        }
+        if ((rc = launch_dirac(lat, lat->scratch_out, lat->scratch_in, prec, st))) return rc;
+        if (host_device_view(out, &out_dev)) {
+            if ((rc = launch_unpack_to_host(lat, out_dev, lat->scratch_out, prec, st))) return rc;
+        } else {
+            if ((rc = launch_unpack(lat, lat->scratch_lex, lat->scratch_out, prec, st))) return rc;
+            QXD_CUDA(cudaMemcpyAsync(out, lat->scratch_lex, bytes, cudaMemcpyDeviceToHost, st));
+        }
         QXD_CUDA(cudaStreamSynchronize(st));
         return QXD_OK;
     }
+    if ((rc = launch_pack(lat, lat->scratch_in, lex_in, prec, st))) return rc;
+    if ((rc = launch_dirac(lat, lat->scratch_out, lat->scratch_in, prec, st))) return rc;
     return launch_unpack(lat, out, lat->scratch_out, prec, st);
 }
 

@@ -273,6 +273,10 @@ int launch_clover_build(qxd_lattice* lat, int* d_bad);
 int launch_dirac(qxd_lattice* lat, void* out, const void* in, int prec, cudaStream_t st);
 int launch_pack(qxd_lattice* lat, void* nat, const void* lex, int prec, cudaStream_t st);
 int launch_unpack(qxd_lattice* lat, void* lex, const void* nat, int prec, cudaStream_t st);
+// page-locked host buffers: device address of p (false for pageable memory)
+bool host_device_view(const void* p, void** dev);
+int launch_pack_from_host(qxd_lattice* lat, void* nat, const void* lex_dev, int prec, cudaStream_t st);
+int launch_unpack_to_host(qxd_lattice* lat, void* lex_dev, const void* nat, int prec, cudaStream_t st);
 int ensure_scratch(qxd_lattice* lat);
 // the lattice that owns the gauge field (the lattice itself unless a view)
 inline qxd_lattice* gauge_owner(qxd_lattice* lat) { return lat->parent ? lat->parent : lat; }

@@ -93,6 +93,16 @@ def test_host_pointer_path_matches_device_path():
         lat.Dw(yd, x.cuda())               # device buffers
         torch.cuda.synchronize()
         assert torch.equal(yh, yd.cpu())
+        # page-locked buffers: read and written by the kernels directly, also
+        # when only one of the two is page-locked
+        xp = x.pin_memory()
+        for yp in (torch.empty_like(x).pin_memory(), torch.empty_like(x)):
+            yp.zero_()
+            lat.Dw(yp, xp)
+            assert torch.equal(yp, yd.cpu())
+        yp = torch.empty_like(x).pin_memory()
+        lat.Dw(yp, x)
+        assert torch.equal(yp, yd.cpu())
     lat.close()
 
 
