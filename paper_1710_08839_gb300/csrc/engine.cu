@@ -29,6 +29,8 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+constexpr long long kBigSites = 1 << 20;  // lattices routed to the single-lattice kernels
+
 // caching device allocator: freed blocks go to per-size free lists
 struct DevicePool {
     std::map<size_t, std::vector<void*>> free_;
@@ -117,6 +119,7 @@ struct Engine {
     BatchReducer red;
     SapJob* d_sap = nullptr;
     int d_sap_cap = 0;
+    SapWork sap_single;  // geometry of the single-lattice Schwarz path
     long long steps = 0;
 
     ~Engine() {
@@ -227,6 +230,12 @@ struct Engine {
         return QXD_OK;
     }
 
+    // jobs on lattices this large fill the GPU alone: their Schwarz method
+    // and D run through the single-lattice kernels (no job-table lookup);
+    // the choice depends only on the job's own lattice, so a job's result
+    // still does not depend on the batch
+    static bool big(const Job* j) { return (long long)j->op->g.V >= kBigSites; }
+
     int step(int* ndone) {
         int rc;
         if ((rc = admit())) return rc;
@@ -259,7 +268,10 @@ struct Engine {
         // phi_k = P(rin)
         std::vector<SapJob> sj;
         for (Job* j : active) {
-            if (j->P.precond == QXD_PRECOND_SAP) {
+            if (j->P.precond == QXD_PRECOND_SAP && big(j)) {
+                if ((rc = sap_apply<float>(j->op, sap_single, j->phi[j->k], j->rin, j->P.sap_ncy, j->P.sap_nmr, st)))
+                    return rc;
+            } else if (j->P.precond == QXD_PRECOND_SAP) {
                 SapJob J{};
                 J.g = j->op->g;
                 J.sg = sap_geom(j->op->g);
@@ -286,7 +298,8 @@ struct Engine {
             std::map<std::pair<int, int>, std::vector<SapJob>> groups;
             size_t idx = 0;
             for (Job* j : active)
-                if (j->P.precond == QXD_PRECOND_SAP) groups[{j->P.sap_ncy, j->P.sap_nmr}].push_back(sj[idx++]);
+                if (j->P.precond == QXD_PRECOND_SAP && !big(j))
+                    groups[{j->P.sap_ncy, j->P.sap_nmr}].push_back(sj[idx++]);
             // the table copies are ordered on the stream, so d_sap can be
             // rewritten for the next group
             for (auto& kv : groups)
@@ -295,10 +308,16 @@ struct Engine {
         // chi_k = D phi_k (FP32)
         {
             std::vector<BatchItem> items;
-            for (Job* j : active) items.push_back(BatchItem{j->op, j->phi[j->k], j->chi[j->k]});
+            for (Job* j : active) {
+                if (big(j)) {
+                    if ((rc = launch_dirac(j->op, j->chi[j->k], j->phi[j->k], QXD_FP32, st))) return rc;
+                } else {
+                    items.push_back(BatchItem{j->op, j->phi[j->k], j->chi[j->k]});
+                }
+            }
             std::stable_sort(items.begin(), items.end(),
                              [](const BatchItem& a, const BatchItem& b) { return a.lat < b.lat; });
-            if ((rc = dw_batch(items, QXD_FP32, 0, st))) return rc;
+            if (!items.empty() && (rc = dw_batch(items, QXD_FP32, 0, st))) return rc;
             for (Job* j : active) ++j->info.inner_calls;
         }
         // Gram-Schmidt: a_j = <chi_j, chi_k>
@@ -441,9 +460,15 @@ struct Engine {
         }
         if ((rc = blas_batch(red, B_UPDATE_X_NATIVE32, (int)upd.size(), 0, st))) return rc;
         std::vector<BatchItem> items;
-        for (Job* j : upd) items.push_back(BatchItem{j->op, j->x64, j->t64});
+        for (Job* j : upd) {
+            if (big(j)) {
+                if ((rc = launch_dirac(j->op, j->t64, j->x64, QXD_FP64, st))) return rc;
+            } else {
+                items.push_back(BatchItem{j->op, j->x64, j->t64});
+            }
+        }
         std::stable_sort(items.begin(), items.end(), [](const BatchItem& a, const BatchItem& b) { return a.lat < b.lat; });
-        if ((rc = dw_batch(items, QXD_FP64, 0, st))) return rc;
+        if (!items.empty() && (rc = dw_batch(items, QXD_FP64, 0, st))) return rc;
         for (size_t i = 0; i < upd.size(); ++i) {
             Job* j = upd[i];
             BJob& b = red.h_jobs[i];

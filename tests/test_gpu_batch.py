@@ -240,3 +240,35 @@ def test_native_layout_solve_matches_lexicographic():
     torch.cuda.synchronize()
     assert torch.equal(x2, x_lex)
     lat.close()
+
+
+def test_engine_large_lattice_path():
+    """Jobs on lattices of 1M sites or more run their Schwarz method and D
+    through the single-lattice kernels: mixed with a small job, the large
+    job's result is the same as alone, and it agrees with qxd_solve."""
+    from paper_1710_08839_gb300 import qxd
+    big = Case(T=48, L1=24, L2=24, L3=24, qhat=2, m0=0.1)           # 1,327,104 sites
+    small = Case(T=8, L1=8, L2=8, L3=8, qhat=-1)
+    lb, ls = big.lattice(), small.lattice()
+    bb = big.psi.to(torch.complex128).cuda().contiguous()
+    bs = small.psi.to(torch.complex128).cuda().contiguous()
+    eng = qxd.Engine(hbm_budget_bytes=64 << 30, max_active=16)
+    xb, xs = torch.zeros_like(bb), torch.zeros_like(bs)
+    ib, i_s = eng.submit(lb, xb, bb, tol=1e-10), eng.submit(ls, xs, bs, tol=1e-10)
+    eng.run()
+    for rid in (ib, i_s):
+        done, info = eng.poll(rid)
+        assert done and info["status"] == qxd.QXD_OK and info["true_relres"] <= 1e-10
+    x1 = torch.zeros_like(bb)
+    rid = eng.submit(lb, x1, bb, tol=1e-10)
+    eng.run()
+    assert eng.poll(rid)[0]
+    eng.close()
+    torch.cuda.synchronize()
+    assert torch.equal(x1, xb)
+    x2 = torch.zeros_like(bb)
+    rc, info = lb.solve(x2, bb, tol=1e-10, precond=qxd.QXD_PRECOND_SAP, inner_prec=qxd.QXD_FP32)
+    assert rc == qxd.QXD_OK
+    assert float((x2 - xb).norm() / x2.norm()) < 1e-8
+    lb.close()
+    ls.close()
