@@ -124,3 +124,21 @@ def test_deflation_state_and_errors(qxd):
     with pytest.raises(qxd.QxdError) as e:
         l2.dfl_subspace(4)
     assert e.value.code == qxd.QXD_ERR_ARG
+
+
+@pytest.mark.slow
+def test_deflated_solve_full_size_near_critical(qxd):
+    """64x64x32x32 doubled lattice near its critical mass (m0 = -0.62, where
+    the SAP solver needs about 40 steps): the deflated solver reaches the same
+    solution with fewer outer steps."""
+    c = Case(T=64, L1=32, L2=32, L3=32, mask=0b1110, qhat=2, m0=-0.62, device="cuda")
+    lat = c.lattice()
+    b = c.psi.to(torch.complex128).cuda().contiguous()
+    x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
+    rc, i1 = lat.solve(x1, b, tol=1e-10, precond=qxd.QXD_PRECOND_SAP, inner_prec=qxd.QXD_FP32)
+    assert rc == qxd.QXD_OK
+    lat.dfl_subspace(16, niter=5, ncy=4, seed=3)
+    rc, i2 = lat.solve(x2, b, tol=1e-10, precond=qxd.QXD_PRECOND_DFL_SAP, inner_prec=qxd.QXD_FP32)
+    assert rc == qxd.QXD_OK and i2["true_relres"] <= 1e-10
+    assert i2["iterations"] < i1["iterations"]
+    assert float((x2 - x1).norm() / x1.norm()) < 1e-8

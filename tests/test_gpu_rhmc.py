@@ -229,3 +229,20 @@ def test_mixed_precision_rational_apply(qxd):
     with pytest.raises(qxd.QxdError) as e:
         lat.rational_apply(out, phi, nu, mu, prec=qxd.QXD_FP32, delta=1.5)
     assert e.value.code == qxd.QXD_ERR_ARG
+
+
+@pytest.mark.slow
+def test_mixed_precision_rational_apply_full_size(qxd):
+    """64x64x32x32 doubled lattice, Table 2's P_1: the FP32-operator path
+    gives the FP64 result (to the tolerance) with true residuals <= tol."""
+    c = Case(T=64, L1=32, L2=32, L3=32, mask=0b1110, qhat=-1, m0=0.05, device="cuda")
+    lat = c.lattice()
+    nu, mu = PR.factor_P(1)
+    phi = c.psi.to(torch.complex128).cuda().contiguous()
+    o64, o32 = torch.empty_like(phi), torch.empty_like(phi)
+    rc, i64 = lat.rational_apply(o64, phi, nu, mu, tol=1e-10)
+    assert rc == qxd.QXD_OK
+    rc, i32 = lat.rational_apply(o32, phi, nu, mu, tol=1e-10, prec=qxd.QXD_FP32)
+    assert rc == qxd.QXD_OK and i32["true_relres"] <= 1e-10
+    assert float((o32 - o64).norm() / o64.norm()) < 1e-9
+    assert abs(i32["action"] - i64["action"]) <= 1e-10 * abs(i64["action"])
