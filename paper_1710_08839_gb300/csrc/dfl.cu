@@ -458,7 +458,6 @@ int build_little(qxd_lattice* lat, DflWork& W, cudaStream_t st) {
     QXD_CUDA(cudaStreamSynchronize(st));
     W.op_version = lat->op_version;
     W.ready = true;
-    (void)BSITES;
     return QXD_OK;
 }
 

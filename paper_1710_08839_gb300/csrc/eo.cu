@@ -157,7 +157,6 @@ enum { EOAPI_DHAT, EOAPI_PREPARE, EOAPI_RECONSTRUCT };
 template <typename R>
 int eo_native(qxd_lattice* lat, int what, void* out, const void* in, void* tmp, cudaStream_t st) {
     const int V = lat->g.V;
-    const size_t half_bytes = (size_t)lat->g.Vh * 24 * sizeof(R);
     int rc;
     if (what == EOAPI_DHAT) {
         // tmp (odd half of a full array) holds M_oo^-1 H_oe in_e
@@ -178,7 +177,6 @@ int eo_native(qxd_lattice* lat, int what, void* out, const void* in, void* tmp, 
     const size_t vb = sizeof(typename Fields<R>::vec);
     for (size_t k = 0; k < comp; ++k)
         QXD_CUDA(cudaMemsetAsync((char*)out + (k * V + lat->g.Vh) * vb, 0, (size_t)lat->g.Vh * vb, st));
-    (void)half_bytes;
     return QXD_OK;
 }
 

@@ -475,7 +475,7 @@ class Lattice:
         return qxd_sw_logdet(self.handle, sites)
 
     @staticmethod
-    def _mscg_params(fields, native, host, kw):
+    def _mscg_params(native, host, kw):
         p = qxd_mscg_defaults()
         for k, v in kw.items():
             if not hasattr(p, k):
@@ -492,7 +492,7 @@ class Lattice:
         complex128 full-lattice tensors). Returns (status, info dict, relres list)."""
         if len(xs) != len(sigmas):
             raise ValueError("one solution tensor per shift")
-        p = self._mscg_params(None, native, b.device.type == "cpu", kw)
+        p = self._mscg_params(native, b.device.type == "cpu", kw)
         rc, info, rel = qxd_mscg(self.handle, list(sigmas), [x.data_ptr() for x in xs], b.data_ptr(), p,
                                  _stream_ptr(stream))
         return rc, info.as_dict(), rel
@@ -500,7 +500,7 @@ class Lattice:
     def rational_apply(self, out, phi, nu, mu, native=False, stream=None, **kw):
         """out = prod_j (A + nu_j^2)/(A + mu_j^2) phi, A = D_hat^dag D_hat.
         Returns (status, info dict); info['action'] = Re <phi, out>."""
-        p = self._mscg_params(None, native, phi.device.type == "cpu", kw)
+        p = self._mscg_params(native, phi.device.type == "cpu", kw)
         rc, info = qxd_rational_apply(self.handle, list(nu), list(mu), out.data_ptr(), phi.data_ptr(), p,
                                       _stream_ptr(stream))
         return rc, info.as_dict()
