@@ -690,12 +690,14 @@ def rational_benchmark(qxd, torch):
 
 
 # Wilson flow of the solver workload's gauge field: FP64 work per RK3 stage
-# and integrated link (staple sum 12 products, W = U S, exp by 10 Horner
-# products, exp(X) U: 24 complex 3x3 products of 198 flops, plus the U(1)
-# angle update), the links integrated being the physical ones (half the
-# simulated lattice with C* boundaries)
+# and integrated link: the staple sum (12 complex 3x3 products of 198 flops),
+# W = U S and exp(X) U (2 more), the exponential by Cayley-Hamilton (X^2: one
+# product; det X ~ 60; 24 terms of the scalar recurrence ~ 26 each; the
+# combination A + B X + C X^2 ~ 144), plus the U(1) angle update (~ 60); the
+# links integrated are the physical ones (half the simulated lattice with C*
+# boundaries)
 FLOW_WORKLOAD = dict(eps=0.02, steps=(5, 5, 10), q_el=1.0 / 6.0)
-FLOW_FLOPS_PER_LINK_STAGE = 24 * 198 + 60
+FLOW_FLOPS_PER_LINK_STAGE = 15 * 198 + 60 + 24 * 26 + 144 + 60
 
 
 def flow_benchmark(qxd, torch):

@@ -82,39 +82,58 @@ __global__ void __launch_bounds__(RED_THREADS) k_gauge_obs(int V, const double* 
 // Wilson flow
 // ---------------------------------------------------------------------------
 
-// exp(X) for anti-Hermitian X: X / 2^k with |X / 2^k|_F <= 1/8, Taylor series
-// of degree 10 by Horner's rule (remainder below 2e-18), then k squarings
-__device__ M3 expm3(const M3& X) {
+// exp(X) for traceless X (the flow's X is anti-Hermitian and traceless). By
+// the Cayley-Hamilton theorem X^3 = d1 X + d0 with d1 = tr(X^2)/2 and
+// d0 = det X, so every power is X^n = a_n + b_n X + c_n X^2 with
+//   a_{n+1} = c_n d0,  b_{n+1} = a_n + c_n d1,  c_{n+1} = b_n,
+// and exp(X) = A + B X + C X^2 with A, B, C the sums of a_n/n!, b_n/n!,
+// c_n/n! (the Taylor series, summed on these scalars). X is first scaled by
+// 2^-k to |X|_F <= 1/2, where 24 terms leave a remainder below 1e-30, and
+// the result squared k times. One 3x3 product (X^2) instead of one per term.
+__device__ M3 expm3(const M3& X0) {
     double n2 = 0.0;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) n2 += X.a[i][j].re * X.a[i][j].re + X.a[i][j].im * X.a[i][j].im;
+        for (int j = 0; j < 3; ++j) n2 += X0.a[i][j].re * X0.a[i][j].re + X0.a[i][j].im * X0.a[i][j].im;
     double nrm = sqrt(n2);
     int k = 0;
-    while (nrm > 0.125 && k < 40) {
+    while (nrm > 0.5 && k < 40) {
         nrm *= 0.5;
         ++k;
     }
     const double sc = ldexp(1.0, -k);
-    M3 Y;
+    M3 X;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) Y.a[i][j] = sc * X.a[i][j];
+        for (int j = 0; j < 3; ++j) X.a[i][j] = sc * X0.a[i][j];
+    const M3 X2 = mul(X, X);
+    const C64 d1 = 0.5 * (X2.a[0][0] + X2.a[1][1] + X2.a[2][2]);
+    const C64 d0 = X.a[0][0] * (X.a[1][1] * X.a[2][2] - X.a[1][2] * X.a[2][1]) -
+                   X.a[0][1] * (X.a[1][0] * X.a[2][2] - X.a[1][2] * X.a[2][0]) +
+                   X.a[0][2] * (X.a[1][0] * X.a[2][1] - X.a[1][1] * X.a[2][0]);
+    // term n: (a, b, c) / n!
+    C64 a = mk(1.0, 0.0), b = mk(0.0, 0.0), c = mk(0.0, 0.0);
+    C64 A = a, B = b, Cc = c;
+#pragma unroll 1
+    for (int n = 0; n < 24; ++n) {
+        const double r = 1.0 / (n + 1);
+        const C64 an = r * (c * d0);
+        const C64 bn = r * (a + c * d1);
+        const C64 cn = r * b;
+        a = an;
+        b = bn;
+        c = cn;
+        A = A + a;
+        B = B + b;
+        Cc = Cc + c;
+    }
     M3 E;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) E.a[i][j] = mk(i == j ? 1.0 : 0.0, 0.0);
-    for (int d = 10; d >= 1; --d) {
-        M3 T = mul(Y, E);
-        const double r = 1.0 / d;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) E.a[i][j] = mk((i == j ? 1.0 : 0.0) + r * T.a[i][j].re, r * T.a[i][j].im);
-    }
+        for (int j = 0; j < 3; ++j) E.a[i][j] = B * X.a[i][j] + Cc * X2.a[i][j] + (i == j ? A : mk(0.0, 0.0));
     for (int i = 0; i < k; ++i) E = mul(E, E);
     return E;
 }
