@@ -438,7 +438,9 @@ int qxd_gauge_observables(qxd_lattice* lat, double q_el, double* out);
  * clover term built from the old field (this lattice's and its views') is
  * stale: qxd_Dw and the solvers return QXD_ERR_STATE until qxd_sw_build.
  * Views cannot flow (QXD_ERR_STATE): flow the lattice that owns the field.
- * Allocates its work fields (about 0.9 KB per site) for the call.
+ * Allocates its work fields (about 0.9 KB per site) for the call; if that
+ * fails (QXD_ERR_OOM) the field is unchanged. A failure after the first step
+ * started leaves the field unusable (QXD_ERR_STATE until qxd_set_gauge).
  * Synchronises the lattice's stream.
  */
 int qxd_wflow(qxd_lattice* lat, double eps, int nsteps);

@@ -387,12 +387,22 @@ int qxd_wflow(qxd_lattice* lat, double eps, int nsteps) {
     cudaFree(Abuf);
     cudaFree(X);
     cudaFree(Xa);
-    if (e != cudaSuccess) return cuda_fail(e, "qxd_wflow");
     // the clover terms of this lattice and its views are now stale
     ++lat->gauge_version;
-    if ((rc = launch_field_tensor(lat))) return rc;
+    if (e != cudaSuccess) {
+        // the field may be part-way through a step: unusable until set again
+        lat->has_gauge = false;
+        return cuda_fail(e, "qxd_wflow");
+    }
+    if ((rc = launch_field_tensor(lat))) {
+        lat->has_gauge = false;
+        return rc;
+    }
     e = cudaStreamSynchronize(lat->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "qxd_wflow: field tensor");
+    if (e != cudaSuccess) {
+        lat->has_gauge = false;
+        return cuda_fail(e, "qxd_wflow: field tensor");
+    }
     return QXD_OK;
 }
 
