@@ -14,6 +14,7 @@
 // Starting from psi = 0, ncy cycles give psi = SAP(eta).
 // The block spinors live in shared memory; links and clover blocks are read
 // from the global fields.
+#include <algorithm>
 #include <vector>
 
 #include "dirac_common.cuh"
@@ -187,8 +188,8 @@ __device__ __noinline__ void residual_at(const Geom& g, const Fields<R>& f, cons
     for (int i = 0; i < 12; ++i) r[i] = r[i] - (w[i] - R(0.5) * acc[i]);
 }
 
-// sum over the 128 threads of the block, result in every thread
-template <typename R>
+// sum over the NT threads of the block, result in every thread
+template <typename R, int NT = SAP_THREADS>
 __device__ __forceinline__ void block_sum3(R a, R b, R c, R* red, R out[3]) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -205,7 +206,7 @@ __device__ __forceinline__ void block_sum3(R a, R b, R c, R* red, R out[3]) {
     __syncthreads();
     out[0] = out[1] = out[2] = R(0);
 #pragma unroll
-    for (int w = 0; w < SAP_THREADS / 32; ++w) {
+    for (int w = 0; w < NT / 32; ++w) {
         out[0] += red[3 * w];
         out[1] += red[3 * w + 1];
         out[2] += red[3 * w + 2];
@@ -372,10 +373,382 @@ __global__ void __launch_bounds__(SAP_THREADS, 2) k_sap_block(Geom g, SapGeom sg
     sap_block_body<R, QNZ>(g, sg, blockIdx.x, colour, psi_zero, f, Cinv, eta, nmr, q);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 block solve with two threads per site pair (spin split)
+//
+// Thread 2t + sg owns the spin-sg half of every block spinor of local pair t:
+// components 3 sg + c (upper chirality) and 6 + 3 sg + c (lower chirality,
+// spin 2 + sg), c = 0..2. In the chiral basis (1 -+ g_mu) psi is fixed by a
+// half spinor (h_0, h_1): the upper spins are U h and the lower ones a fixed
+// 2x2 spin matrix times U h. Thread sg forms h_sg from two spin components of
+// the neighbour, multiplies it by the link, and adds U h_sg to its own upper
+// spin and to one lower spin: its own (mu = 0, 3) or its partner's
+// (mu = 1, 2). The partner's share is exchanged once per hop set with a warp
+// shuffle. The clover term acts within a chirality, so each thread computes
+// its three rows of both 6x6 blocks after one shuffle of the partner's half.
+// The arithmetic per block is that of the one-thread-per-pair form, spread
+// over twice the threads at about half the registers each.
+// ---------------------------------------------------------------------------
+constexpr int SPLIT_THREADS = 256;
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+// Shared-memory fields keep the [24][128] layout of SmemField, with the
+// slots of spins 1 and 3 rotated by 16: the two threads of a pair read the
+// same slot in spins of opposite parity, which then fall in different banks.
+__device__ __forceinline__ const float* spin_ptr(const float* a, int spin, int slot) {
+    return a + 6 * spin * SAP_HALF + ((slot + 16 * (spin & 1)) & (SAP_HALF - 1));
+}
+__device__ __forceinline__ void ld_spin(const float* a, int spin, int slot, cplx<float> v[3]) {
+    const float* p = spin_ptr(a, spin, slot);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = mk(p[(2 * c) * SAP_HALF], p[(2 * c + 1) * SAP_HALF]);
+}
+__device__ __forceinline__ void st_spin(float* a, int spin, int slot, const cplx<float> v[3]) {
+    float* p = const_cast<float*>(spin_ptr(a, spin, slot));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        p[(2 * c) * SAP_HALF] = v[c].re;
+        p[(2 * c + 1) * SAP_HALF] = v[c].im;
+    }
+}
+// own half: v[0..2] spin sg, v[3..5] spin 2 + sg
+__device__ __forceinline__ void ld_half(const float* a, int sg, int slot, cplx<float> v[6]) {
+    ld_spin(a, sg, slot, v);
+    ld_spin(a, 2 + sg, slot, v + 3);
+}
+__device__ __forceinline__ void st_half(float* a, int sg, int slot, const cplx<float> v[6]) {
+    st_spin(a, sg, slot, v);
+    st_spin(a, 2 + sg, slot, v + 3);
+}
+__device__ __forceinline__ void ld_full(const float* a, int slot, cplx<float> v[12]) {
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) ld_spin(a, sp, slot, v + 3 * sp);
+}
+__device__ __forceinline__ void st_full(float* a, int slot, const cplx<float> v[12]) {
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) st_spin(a, sp, slot, v + 3 * sp);
+}
+
+// Block links of the split kernel in shared memory. The block operator uses
+// only the links that stay inside the block, those of sites with l[mu] < 3,
+// 192 per direction. Entry of the site of parity p and local index lidx in
+// direction mu (stride S = 64, 16, 4, 1 in lidx):
+//   mu = 0, 1, 2: p * 96 + compact pair slot, with the pair slot lidx >> 1
+//                 written as hi * 2S + l * S/2 + lo (l = l[mu]) and compacted to
+//                 hi * 3S/2 + l * S/2 + lo, so that consecutive pairs read
+//                 consecutive entries;
+//   mu = 3:       3 (lidx >> 2) + (lidx & 3).
+constexpr int SPLIT_LINKS = 192;  // interior links per direction
+
+template <int MU>
+__device__ __forceinline__ int link_entry(int p, int lidx) {
+    if constexpr (MU == 3) {
+        return 3 * (lidx >> 2) + (lidx & 3);
+    } else {
+        constexpr int H = MU == 0 ? 32 : MU == 1 ? 8 : 2;  // S / 2
+        const int slot = lidx >> 1;
+        return p * (SPLIT_LINKS / 2) + (slot / (4 * H)) * (3 * H) + ((slot / H) & 3) * H + (slot & (H - 1));
+    }
+}
+
+struct SplitLinks {
+    const float4* U;  // [4][3][192] two rows
+    const float2* Z;  // [4][192] z^qhat
+    __device__ __forceinline__ void link(int mu, int e, cplx<float> u[3][3]) const {
+        const float4 a = U[(mu * 3 + 0) * SPLIT_LINKS + e];
+        const float4 b = U[(mu * 3 + 1) * SPLIT_LINKS + e];
+        const float4 c = U[(mu * 3 + 2) * SPLIT_LINKS + e];
+        u[0][0] = mk(a.x, a.y);
+        u[0][1] = mk(a.z, a.w);
+        u[0][2] = mk(b.x, b.y);
+        u[1][0] = mk(b.z, b.w);
+        u[1][1] = mk(c.x, c.y);
+        u[1][2] = mk(c.z, c.w);
+        u[2][0] = conj(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
+        u[2][1] = conj(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
+        u[2][2] = conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+    }
+    __device__ __forceinline__ cplx<float> phase(int mu, int e) const {
+        const float2 z = Z[mu * SPLIT_LINKS + e];
+        return mk(z.x, z.y);
+    }
+};
+
+constexpr size_t split_link_bytes() { return 12 * SPLIT_LINKS * sizeof(float4) + 4 * SPLIT_LINKS * sizeof(float2); }
+
+// Hops of direction MU inside the block for thread sg (sgn = +1 for sg = 0,
+// -1 for sg = 1). With a the neighbour's spin sg and b the lower spin named
+// below, h_sg = a + DIR c_MU b with c_0 = 1, c_1 = i, c_2 = sgn, c_3 = sgn i;
+// g = U h_sg (U^+ backwards) goes to au (upper spin sg) and, times
+// DIR, 1 / -i / sgn / -sgn i for MU = 0..3, to al (lower spin 2 + sg, MU =
+// 0, 3) or ax (lower spin 3 - sg, the partner's, MU = 1, 2).
+template <bool QNZ, int MU>
+__device__ __forceinline__ void split_dir(const SplitLinks& bl, const float* src, const Site& t, int p, int sg,
+                                          float sgn, cplx<float> au[3], cplx<float> al[3], cplx<float> ax[3]) {
+    constexpr int stride = MU == 0 ? 64 : MU == 1 ? 16 : MU == 2 ? 4 : 1;
+    const int lspin = (MU == 0 || MU == 3) ? 2 + sg : 3 - sg;
+    cplx<float> a[3], b[3], h[3], gv[3], u[3][3];
+    if (t.l[MU] < SAP_BS - 1) {
+        const int slot = (t.lidx + stride) >> 1;
+        ld_spin(src, sg, slot, a);
+        ld_spin(src, lspin, slot, b);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (MU == 0) h[c] = a[c] + b[c];
+            else if (MU == 1) h[c] = a[c] + times_i(b[c]);
+            else if (MU == 2) h[c] = a[c] + sgn * b[c];
+            else h[c] = a[c] + sgn * times_i(b[c]);
+        }
+        const int e = link_entry<MU>(p, t.lidx);
+        bl.link(MU, e, u);
+        su3_mul(u, h, gv);
+        if (QNZ) times3(bl.phase(MU, e), gv);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            au[c] = au[c] + gv[c];
+            if (MU == 0) al[c] = al[c] + gv[c];
+            else if (MU == 1) ax[c] = ax[c] + times_mi(gv[c]);
+            else if (MU == 2) ax[c] = ax[c] + sgn * gv[c];
+            else al[c] = al[c] - sgn * times_i(gv[c]);
+        }
+    }
+    if (t.l[MU] > 0) {
+        const int slot = (t.lidx - stride) >> 1;
+        ld_spin(src, sg, slot, a);
+        ld_spin(src, lspin, slot, b);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (MU == 0) h[c] = a[c] - b[c];
+            else if (MU == 1) h[c] = a[c] - times_i(b[c]);
+            else if (MU == 2) h[c] = a[c] - sgn * b[c];
+            else h[c] = a[c] - sgn * times_i(b[c]);
+        }
+        const int e = link_entry<MU>(1 - p, t.lidx - stride);  // link of the neighbour (other parity)
+        bl.link(MU, e, u);
+        su3_dag_mul(u, h, gv);
+        if (QNZ) times3(conj(bl.phase(MU, e)), gv);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            au[c] = au[c] + gv[c];
+            if (MU == 0) al[c] = al[c] - gv[c];
+            else if (MU == 1) ax[c] = ax[c] + times_i(gv[c]);
+            else if (MU == 2) ax[c] = ax[c] - sgn * gv[c];
+            else al[c] = al[c] + sgn * times_i(gv[c]);
+        }
+    }
+}
+
+// raw block-hop sum at site t, own half (acc[0..2] spin sg, acc[3..5] spin 2 + sg);
+// every thread of the warp must call it (one shuffle at the end)
+// (site t of parity p)
+template <bool QNZ>
+__device__ __forceinline__ void split_hops(const SplitLinks& bl, const float* src, const Site& t, int p, int sg,
+                                           float sgn, cplx<float> acc[6]) {
+    cplx<float> au[3], al[3], ax[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) au[c] = al[c] = ax[c] = mk(0.f, 0.f);
+    split_dir<QNZ, 0>(bl, src, t, p, sg, sgn, au, al, ax);
+    split_dir<QNZ, 1>(bl, src, t, p, sg, sgn, au, al, ax);
+    split_dir<QNZ, 2>(bl, src, t, p, sg, sgn, au, al, ax);
+    split_dir<QNZ, 3>(bl, src, t, p, sg, sgn, au, al, ax);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float xr = __shfl_xor_sync(FULL_MASK, ax[c].re, 1);
+        const float xi = __shfl_xor_sync(FULL_MASK, ax[c].im, 1);
+        acc[c] = au[c];
+        acc[3 + c] = al[c] + mk(xr, xi);
+    }
+}
+
+// Own rows (3 sg + a, a = 0..2) of both packed Hermitian 6x6 blocks of C at
+// site s times v; v and y are own halves, the partner's half is shuffled in.
+// In block order the rows of thread sg see a Hermitian 3x3 diagonal block
+// (entries d[3 sg + a] and L(3 sg + a, 3 sg + b)) and the off-diagonal
+// 3x3 block B[a][b] = L(3 + a, b) for sg = 1, B^+ for sg = 0. Every thread
+// of the warp must call it.
+__device__ __forceinline__ void clover_half(const float4* __restrict__ C, int V, int s, int sg, float sgn,
+                                            const cplx<float> v[6], cplx<float> y[6]) {
+    cplx<float> p[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) p[k] = mk(__shfl_xor_sync(FULL_MASK, v[k].re, 1), __shfl_xor_sync(FULL_MASK, v[k].im, 1));
+#pragma unroll
+    for (int blk = 0; blk < 2; ++blk) {
+        const float4* Cb = C + (size_t)(9 * blk) * V + s;
+        const float4 q0 = Cb[0], q1 = Cb[(size_t)V], q3 = Cb[(size_t)3 * V], q4 = Cb[(size_t)4 * V];
+        const float4 q5 = Cb[(size_t)5 * V], q6 = Cb[(size_t)6 * V], q7 = Cb[(size_t)7 * V];
+        const float4 X = Cb[(size_t)(sg ? 8 : 2) * V];
+        // packed floats: d_i at i, L_k at (6 + 2k, 7 + 2k); float4 n holds 4n..4n+3
+        const float d0 = sg ? q0.w : q0.x, d1 = sg ? q1.x : q0.y, d2 = sg ? q1.y : q0.z;
+        const cplx<float> l10 = sg ? mk(q6.x, q6.y) : mk(q1.z, q1.w);  // L(4,3) : L(1,0)
+        const cplx<float> l20 = mk(X.x, X.y);                          // L(5,3) : L(2,0)
+        const cplx<float> l21 = mk(X.z, X.w);                          // L(5,4) : L(2,1)
+        const cplx<float> B[3][3] = {{mk(q3.x, q3.y), mk(q3.z, q3.w), mk(q4.x, q4.y)},
+                                     {mk(q4.z, q4.w), mk(q5.x, q5.y), mk(q5.z, q5.w)},
+                                     {mk(q6.z, q6.w), mk(q7.x, q7.y), mk(q7.z, q7.w)}};
+        const cplx<float>* w = v + 3 * blk;
+        const cplx<float>* pp = p + 3 * blk;
+        cplx<float> z[3];
+        z[0] = d0 * w[0] + cmul(l10, w[1]) + cmul(l20, w[2]);
+        z[1] = l10 * w[0] + d1 * w[1] + cmul(l21, w[2]);
+        z[2] = l20 * w[0] + l21 * w[1] + d2 * w[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                // E[a][b] = sg ? B[a][b] : conj(B[b][a])
+                const cplx<float> e = mk(sg ? B[a][b].re : B[b][a].re, sg ? B[a][b].im : -B[b][a].im);
+                z[a] = z[a] + e * pp[b];
+            }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) y[3 * blk + a] = z[a];
+    }
+    (void)sgn;
+}
+
+// Same phases as sap_block_body, with the site-pair work split over the
+// two threads of a pair. The residual is computed one site per thread.
+template <bool QNZ>
+__device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm, int bidx, int colour, int psi_zero,
+                                               const Fields<float>& f, const float4* __restrict__ Cinv,
+                                               const float4* __restrict__ eta, int nmr, float q) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* sU = reinterpret_cast<float4*>(smem_raw);
+    float2* sZ = reinterpret_cast<float2*>(smem_raw + 12 * SPLIT_LINKS * sizeof(float4));
+    const SplitLinks bl{sU, sZ};
+    float* sm = reinterpret_cast<float*>(smem_raw + split_link_bytes());
+    float* s_ro = sm;                   // r on the odd sites, then delta_o
+    float* s_rho = sm + 24 * SAP_HALF;  // r on the even sites, then the MR residual
+    float* s_t = sm + 48 * SAP_HALF;    // odd temporary / delta_e at the end
+    float* red = sm + 72 * SAP_HALF;    // 3 * warps reduction slots
+
+    int org[4];
+    {
+        const int bi2 = 2 * bidx;
+        const int b3e = bi2 % sgm.nb3;
+        int rest = bi2 / sgm.nb3;
+        const int b2 = rest % sgm.nb2;
+        rest /= sgm.nb2;
+        const int b1 = rest % sgm.nb1;
+        const int b0 = rest / sgm.nb1;
+        const int b3 = b3e + ((b0 + b1 + b2 + b3e + colour) & 1);
+        org[0] = SAP_BS * b0;
+        org[1] = SAP_BS * b1;
+        org[2] = SAP_BS * b2;
+        org[3] = SAP_BS * b3;
+    }
+    const int t = threadIdx.x >> 1;
+    const int sg = threadIdx.x & 1;
+    const float sgn = sg ? -1.f : 1.f;
+    const int base = 2 * t;
+    const int par0 = ((base >> 6) + ((base >> 4) & 3) + ((base >> 2) & 3) + (base & 3)) & 1;
+    const Site se = make_site(g, org, base + par0);
+    const Site so = make_site(g, org, base + 1 - par0);
+    const Site& me = sg ? so : se;  // the site this thread stages, and whose residual it computes
+
+    // interior links of this thread's site (se has parity 0, so parity 1)
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        if (me.l[mu] == SAP_BS - 1) continue;
+        const int e = mu == 0   ? link_entry<0>(sg, me.lidx)
+                      : mu == 1 ? link_entry<1>(sg, me.lidx)
+                      : mu == 2 ? link_entry<2>(sg, me.lidx)
+                                : link_entry<3>(sg, me.lidx);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) sU[(mu * 3 + j) * SPLIT_LINKS + e] = f.U[((size_t)mu * 3 + j) * g.V + me.s];
+        const cplx<float> z = QNZ ? link_phase(f.A, g.V, mu, me.s, q) : mk(1.f, 0.f);
+        sZ[mu * SPLIT_LINKS + e] = make_float2(z.re, z.im);
+    }
+
+    {
+        cplx<float> r[12];
+        residual_at<float, QNZ>(g, f, eta, q, me, psi_zero, r);
+        st_full(sg ? s_ro : s_rho, t, r);
+    }
+    __syncthreads();
+
+    cplx<float> v[6], w[6], acc[6], rho[6];
+    ld_half(s_ro, sg, t, v);
+    clover_half(Cinv, g.V, so.s, sg, sgn, v, w);  // t_o = M_oo^-1 r_o
+    st_half(s_t, sg, t, w);
+    __syncthreads();
+
+    // rho stays in shared memory between steps (fewer live registers)
+    cplx<float> de[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) de[i] = mk(0.f, 0.f);
+    const int nsteps = 2 * nmr + 2;
+#pragma unroll 1
+    for (int step = 0; step < nsteps; ++step) {
+        const bool odd = (step & 1) != 0;
+        const bool last = step == nsteps - 1;
+        split_hops<QNZ>(bl, odd ? (last ? s_t : s_rho) : s_t, odd ? so : se, odd ? 1 : 0, sg, sgn, acc);
+        if (step == 0) {
+            ld_half(s_rho, sg, t, rho);  // r_e
+#pragma unroll
+            for (int i = 0; i < 6; ++i) rho[i] = rho[i] + 0.5f * acc[i];
+            st_half(s_rho, sg, t, rho);
+        } else if (last) {
+            ld_half(s_ro, sg, t, v);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) v[i] = v[i] + 0.5f * acc[i];
+            clover_half(Cinv, g.V, so.s, sg, sgn, v, w);  // delta_o
+            st_half(s_ro, sg, t, w);
+        } else if (odd) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) v[i] = -0.5f * acc[i];
+            clover_half(Cinv, g.V, so.s, sg, sgn, v, w);
+            st_half(s_t, sg, t, w);
+        } else {
+            ld_half(s_rho, sg, t, rho);
+            clover_half(f.C, g.V, se.s, sg, sgn, rho, w);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) w[i] = w[i] + 0.5f * acc[i];
+            float a_re = 0.f, a_im = 0.f, b = 0.f;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                a_re += w[i].re * rho[i].re + w[i].im * rho[i].im;
+                a_im += w[i].re * rho[i].im - w[i].im * rho[i].re;
+                b += w[i].re * w[i].re + w[i].im * w[i].im;
+            }
+            float sums[3];
+            block_sum3<float, SPLIT_THREADS>(a_re, a_im, b, red, sums);
+            if (sums[2] > 0.f) {  // else rho = 0 on the whole block: nothing to add
+                const cplx<float> om = mk(sums[0] / sums[2], sums[1] / sums[2]);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    de[i] = de[i] + om * rho[i];
+                    rho[i] = rho[i] - om * w[i];
+                }
+            }
+            if (step == nsteps - 2) st_half(s_t, sg, t, de);  // delta_e for the last step
+            else st_half(s_rho, sg, t, rho);
+        }
+        __syncthreads();
+    }
+    // psi_B += delta on this thread's site: delta_e in s_t, delta_o in s_ro
+    cplx<float> d[12];
+    ld_full(sg ? s_ro : s_t, t, d);
+    float4* psi = const_cast<float4*>(f.psi);
+    if (!psi_zero) {
+        cplx<float> o[12];
+        load_spinor(f.psi, g.V, me.s, o);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) d[i] = d[i] + o[i];
+    }
+    store_spinor(psi, g.V, me.s, d);
+}
+
+template <bool QNZ>
+__global__ void __launch_bounds__(SPLIT_THREADS, 2) k_sap_split(Geom g, SapGeom sgm, int colour, int psi_zero,
+                                                                Fields<float> f, const float4* __restrict__ Cinv,
+                                                                const float4* __restrict__ eta, int nmr, float q) {
+    sap_split_body<QNZ>(g, sgm, blockIdx.x, colour, psi_zero, f, Cinv, eta, nmr, q);
+}
+
 // batched form: thread block b works on block (b - cta_begin) of the job
 // whose range holds b (one launch serves every job of a batch)
-__global__ void __launch_bounds__(SAP_THREADS, 2) k_sap_block_batch(const SapJob* __restrict__ jobs, int njobs,
-                                                                    int colour, int psi_zero, int nmr) {
+__global__ void __launch_bounds__(SPLIT_THREADS, 2) k_sap_block_batch(const SapJob* __restrict__ jobs, int njobs,
+                                                                      int colour, int psi_zero, int nmr) {
     int lo = 0, hi = njobs - 1;
     const int b = blockIdx.x;
     while (lo < hi) {
@@ -384,12 +757,31 @@ __global__ void __launch_bounds__(SAP_THREADS, 2) k_sap_block_batch(const SapJob
         else hi = mid - 1;
     }
     const SapJob& J = jobs[lo];
-    sap_block_body<float, true>(J.g, J.sg, b - J.cta_begin, colour, psi_zero, J.f, J.Cinv, J.eta, nmr, J.q);
+    sap_split_body<true>(J.g, J.sg, b - J.cta_begin, colour, psi_zero, J.f, J.Cinv, J.eta, nmr, J.q);
 }
 
 template <typename R>
 size_t sap_smem_bytes() {
+    if (sizeof(R) == 4)  // split kernel: interior links, three block fields, reduction slots of 8 warps
+        return split_link_bytes() + (72 * SAP_HALF + 3 * (SPLIT_THREADS / 32)) * sizeof(R);
     return sap_link_bytes<R>() + (72 * SAP_HALF + 3 * (SAP_THREADS / 32)) * sizeof(R);
+}
+
+// Dynamic shared memory of the split kernel, and an L1/shared carveout just
+// large enough for two blocks per SM: the rest of the SM's L1 caches the
+// clover blocks that every MR step re-reads.
+template <typename K>
+int split_attrs(K kernel, size_t smem) {
+    int dev = 0, per_sm = 0;
+    QXD_CUDA(cudaGetDevice(&dev));
+    QXD_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    QXD_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (per_sm > 0) {
+        const long need = 2L * ((long)smem + 1024);
+        const int pct = (int)std::min(100L, (100 * need + per_sm - 1) / per_sm);
+        QXD_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+    }
+    return QXD_OK;
 }
 
 template <typename R, bool QNZ>
@@ -397,10 +789,18 @@ int launch_sap_block(qxd_lattice* lat, const SapGeom& sg, int colour, int psi_ze
                      const typename Fields<R>::cvec* Cinv, const typename Fields<R>::vec* eta, int nmr,
                      cudaStream_t st) {
     const size_t smem = sap_smem_bytes<R>();
-    QXD_CUDA(cudaFuncSetAttribute(k_sap_block<R, QNZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_sap_block<R, QNZ><<<sg.nhalf, SAP_THREADS, smem, st>>>(lat->g, sg, colour, psi_zero, f, Cinv, eta, nmr,
-                                                              (R)lat->qhat);
-    QXD_LAUNCHED("k_sap_block");
+    if constexpr (sizeof(R) == 4) {
+        int rc = split_attrs(k_sap_split<QNZ>, smem);
+        if (rc) return rc;
+        k_sap_split<QNZ><<<sg.nhalf, SPLIT_THREADS, smem, st>>>(lat->g, sg, colour, psi_zero, f, Cinv, eta, nmr,
+                                                                (float)lat->qhat);
+        QXD_LAUNCHED("k_sap_split");
+    } else {
+        QXD_CUDA(cudaFuncSetAttribute(k_sap_block<R, QNZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_sap_block<R, QNZ><<<sg.nhalf, SAP_THREADS, smem, st>>>(lat->g, sg, colour, psi_zero, f, Cinv, eta, nmr,
+                                                                  (R)lat->qhat);
+        QXD_LAUNCHED("k_sap_block");
+    }
     return QXD_OK;
 }
 
@@ -488,11 +888,12 @@ int sap_apply_batch(std::vector<SapJob>& jobs, SapJob* d_jobs, int ncy, int nmr,
     }
     QXD_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(SapJob), cudaMemcpyHostToDevice, st));
     const size_t smem = sap_smem_bytes<float>();
-    QXD_CUDA(cudaFuncSetAttribute(k_sap_block_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int rc = split_attrs(k_sap_block_batch, smem);
+    if (rc) return rc;
     for (int cy = 0; cy < ncy; ++cy)
         for (int colour = 0; colour < 2; ++colour) {
             const int psi_zero = (cy == 0 && colour == 0) ? 1 : 0;
-            k_sap_block_batch<<<ctas, SAP_THREADS, smem, st>>>(d_jobs, (int)jobs.size(), colour, psi_zero, nmr);
+            k_sap_block_batch<<<ctas, SPLIT_THREADS, smem, st>>>(d_jobs, (int)jobs.size(), colour, psi_zero, nmr);
             QXD_LAUNCHED("k_sap_block_batch");
         }
     return QXD_OK;
