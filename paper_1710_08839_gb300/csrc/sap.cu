@@ -169,8 +169,8 @@ __device__ __forceinline__ void block_hops(const Geom& g, const Fields<R>& f, co
 
 // r = eta - (D psi)(x), D over the whole lattice, at one site
 template <typename R, bool QNZ>
-__device__ __noinline__ void residual_at(const Geom& g, const Fields<R>& f, const typename Fields<R>::vec* eta,
-                                         R q, const Site& t, bool psi_zero, cplx<R> r[12]) {
+__device__ __forceinline__ void residual_body(const Geom& g, const Fields<R>& f, const typename Fields<R>::vec* eta,
+                                              R q, const Site& t, bool psi_zero, cplx<R> r[12]) {
     load_spinor(eta, g.V, t.s, r);
     if (psi_zero) return;
     const int po = 1 - ((t.x[0] + t.x[1] + t.x[2] + t.x[3]) & 1);
@@ -186,6 +186,13 @@ __device__ __noinline__ void residual_at(const Geom& g, const Fields<R>& f, cons
     clover_mul(f.C, g.V, t.s, v, w);
 #pragma unroll
     for (int i = 0; i < 12; ++i) r[i] = r[i] - (w[i] - R(0.5) * acc[i]);
+}
+
+// out-of-line form for the one-thread-per-pair kernel, which calls it twice
+template <typename R, bool QNZ>
+__device__ __noinline__ void residual_at(const Geom& g, const Fields<R>& f, const typename Fields<R>::vec* eta,
+                                         R q, const Site& t, bool psi_zero, cplx<R> r[12]) {
+    residual_body<R, QNZ>(g, f, eta, q, t, psi_zero, r);
 }
 
 // sum over the NT threads of the block, result in every thread
@@ -661,7 +668,7 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
 
     {
         cplx<float> r[12];
-        residual_at<float, QNZ>(g, f, eta, q, me, psi_zero, r);
+        residual_body<float, QNZ>(g, f, eta, q, me, psi_zero, r);
         st_full(sg ? s_ro : s_rho, t, r);
     }
     __syncthreads();
