@@ -195,8 +195,10 @@ __device__ __noinline__ void residual_at(const Geom& g, const Fields<R>& f, cons
     residual_body<R, QNZ>(g, f, eta, q, t, psi_zero, r);
 }
 
-// sum over the NT threads of the block, result in every thread
-template <typename R, int NT = SAP_THREADS>
+// sum over the NT threads of the block, result in every thread. TAIL_SYNC
+// guards red against the next call; a caller that passes a barrier before it
+// reuses red may drop it.
+template <typename R, int NT = SAP_THREADS, bool TAIL_SYNC = true>
 __device__ __forceinline__ void block_sum3(R a, R b, R c, R* red, R out[3]) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -218,7 +220,7 @@ __device__ __forceinline__ void block_sum3(R a, R b, R c, R* red, R out[3]) {
         out[1] += red[3 * w + 1];
         out[2] += red[3 * w + 2];
     }
-    __syncthreads();
+    if (TAIL_SYNC) __syncthreads();
 }
 
 template <typename R>
@@ -718,7 +720,8 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
                 b += w[i].re * w[i].re + w[i].im * w[i].im;
             }
             float sums[3];
-            block_sum3<float, SPLIT_THREADS>(a_re, a_im, b, red, sums);
+            // red is next written two steps later, after the barriers that end each step
+            block_sum3<float, SPLIT_THREADS, false>(a_re, a_im, b, red, sums);
             if (sums[2] > 0.f) {  // else rho = 0 on the whole block: nothing to add
                 const cplx<float> om = mk(sums[0] / sums[2], sums[1] / sums[2]);
 #pragma unroll
