@@ -320,6 +320,11 @@ int qxd_engine_forget(qxd_engine* e, long long id);
 int qxd_engine_run(qxd_engine* e);
 /* device bytes of active requests, bytes held by the allocator, steps so far */
 int qxd_engine_stats(const qxd_engine* e, size_t* bytes_in_use, size_t* bytes_held, long long* steps);
+/* CUDA graphs of the batched Schwarz launch sets (lattices under 2^20 sites):
+ * captures made and replays of a captured graph so far. A set is captured on
+ * its first use and replayed while the job table, job count, CTA count, ncy
+ * and nmr stay the same. Either pointer may be NULL. */
+int qxd_engine_graph_stats(const qxd_engine* e, long long* captures, long long* replays);
 
 /* ---------------------------------------------------------------------------
  * Pseudofermion action of the RHMC (Sec. 2.4):

@@ -119,10 +119,12 @@ struct Engine {
     BatchReducer red;
     SapJob* d_sap = nullptr;
     int d_sap_cap = 0;
+    SapGraphCache sap_graphs;  // graphs of the batched SAP launch sets
     SapWork sap_single;  // geometry of the single-lattice Schwarz path
     long long steps = 0;
 
     ~Engine() {
+        sap_graphs.release();
         if (d_sap) cudaFree(d_sap);
         red.release();
         for (auto& kv : jobs) free_job(kv.second.get());
@@ -288,6 +290,7 @@ struct Engine {
             if ((int)sj.size() > d_sap_cap) {
                 if (d_sap) {
                     cudaStreamSynchronize(st);
+                    sap_graphs.clear();  // they hold the old table address
                     cudaFree(d_sap);
                 }
                 d_sap_cap = (int)sj.size() * 2;
@@ -303,7 +306,8 @@ struct Engine {
             // the table copies are ordered on the stream, so d_sap can be
             // rewritten for the next group
             for (auto& kv : groups)
-                if ((rc = sap_apply_batch(kv.second, d_sap, kv.first.first, kv.first.second, st))) return rc;
+                if ((rc = sap_apply_batch(kv.second, d_sap, kv.first.first, kv.first.second, st, &sap_graphs)))
+                    return rc;
         }
         // chi_k = D phi_k (FP32)
         {
@@ -600,6 +604,13 @@ int qxd_engine_stats(const qxd_engine* e, size_t* bytes_in_use, size_t* bytes_he
     if (bytes_in_use) *bytes_in_use = e->pool.in_use;
     if (bytes_held) *bytes_held = e->pool.held;
     if (steps) *steps = e->steps;
+    return QXD_OK;
+}
+
+int qxd_engine_graph_stats(const qxd_engine* e, long long* captures, long long* replays) {
+    if (!e) return fail(QXD_ERR_ARG, "qxd_engine_graph_stats: NULL engine");
+    if (captures) *captures = e->sap_graphs.captures;
+    if (replays) *replays = e->sap_graphs.replays;
     return QXD_OK;
 }
 

@@ -630,7 +630,8 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
     float* s_t = sm + 48 * SAP_HALF;    // odd temporary / delta_e at the end
     float* red = sm + 72 * SAP_HALF;    // 3 * warps reduction slots
 
-    int org[4];
+    // blocks (b0, b1, b2, b3e) and (.., b3e + 1), b3e even: one of each colour
+    int org[4], org3_other;
     {
         const int bi2 = 2 * bidx;
         const int b3e = bi2 % sgm.nb3;
@@ -644,6 +645,7 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
         org[1] = SAP_BS * b1;
         org[2] = SAP_BS * b2;
         org[3] = SAP_BS * b3;
+        org3_other = SAP_BS * (2 * b3e + 1 - b3);
     }
     const int t = threadIdx.x >> 1;
     const int sg = threadIdx.x & 1;
@@ -653,6 +655,17 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
     const Site se = make_site(g, org, base + par0);
     const Site so = make_site(g, org, base + 1 - par0);
     const Site& me = sg ? so : se;  // the site this thread stages, and whose residual it computes
+
+    // psi starts at zero. The first launch (colour 0) neither reads psi nor
+    // writes outside its blocks, so it also clears the partner block of the
+    // other colour, whose psi the next launch reads: no separate memset.
+    if (psi_zero) {
+        const int o2[4] = {org[0], org[1], org[2], org3_other};
+        const Site z = make_site(g, o2, me.lidx);
+        float4* pz = const_cast<float4*>(f.psi);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) pz[(size_t)k * g.V + z.s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 
     // interior links of this thread's site (se has parity 0, so parity 1)
 #pragma unroll
@@ -863,7 +876,8 @@ int sap_apply(qxd_lattice* lat, SapWork& w, void* out, const void* in, int ncy, 
     const bool qnz = lat->qhat != 0;
     // psi starts at zero: the first half-cycle writes the blocks of colour 0
     // without reading psi, and the blocks of colour 1 must read zeros there
-    QXD_CUDA(cudaMemsetAsync(out, 0, (size_t)g.V * 24 * sizeof(R), st));
+    // (the FP32 kernel clears them itself in its first launch)
+    if (sizeof(R) == 8) QXD_CUDA(cudaMemsetAsync(out, 0, (size_t)g.V * 24 * sizeof(R), st));
     int rc;
     for (int cy = 0; cy < ncy; ++cy)
         for (int colour = 0; colour < 2; ++colour) {
@@ -888,24 +902,87 @@ SapGeom sap_geom(const Geom& g) {
     return sg;
 }
 
-int sap_apply_batch(std::vector<SapJob>& jobs, SapJob* d_jobs, int ncy, int nmr, cudaStream_t st) {
+void SapGraphCache::clear() {
+    for (auto& e : entries) cudaGraphExecDestroy(e.exec);
+    entries.clear();
+}
+
+void SapGraphCache::release() {
+    clear();
+    if (cap) cudaStreamDestroy(cap);
+    cap = nullptr;
+}
+
+namespace {
+
+void launch_batch_set(const SapJob* d_jobs, int njobs, int ctas, int ncy, int nmr, size_t smem, cudaStream_t st) {
+    for (int cy = 0; cy < ncy; ++cy)
+        for (int colour = 0; colour < 2; ++colour) {
+            const int psi_zero = (cy == 0 && colour == 0) ? 1 : 0;
+            k_sap_block_batch<<<ctas, SPLIT_THREADS, smem, st>>>(d_jobs, njobs, colour, psi_zero, nmr);
+        }
+}
+
+// the executable graph of this launch set, captured on first use
+int batch_graph(SapGraphCache& gc, const SapJob* d_jobs, int njobs, int ctas, int ncy, int nmr, size_t smem,
+                cudaGraphExec_t* out) {
+    ++gc.tick;
+    for (auto& e : gc.entries)
+        if (e.table == d_jobs && e.njobs == njobs && e.ctas == ctas && e.ncy == ncy && e.nmr == nmr) {
+            e.last = gc.tick;
+            ++gc.replays;
+            *out = e.exec;
+            return QXD_OK;
+        }
+    if (!gc.cap) QXD_CUDA(cudaStreamCreateWithFlags(&gc.cap, cudaStreamNonBlocking));
+    QXD_CUDA(cudaStreamBeginCapture(gc.cap, cudaStreamCaptureModeThreadLocal));
+    launch_batch_set(d_jobs, njobs, ctas, ncy, nmr, smem, gc.cap);
+    const cudaError_t le = cudaGetLastError();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(gc.cap, &graph);  // always ends the capture
+    if (le != cudaSuccess || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(le != cudaSuccess ? le : ce, "k_sap_block_batch graph capture");
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate (SAP launch set)");
+    if ((int)gc.entries.size() >= SapGraphCache::kMax) {
+        auto lru = std::min_element(gc.entries.begin(), gc.entries.end(),
+                                    [](const SapGraphCache::Entry& a, const SapGraphCache::Entry& b) { return a.last < b.last; });
+        cudaGraphExecDestroy(lru->exec);
+        gc.entries.erase(lru);
+    }
+    gc.entries.push_back(SapGraphCache::Entry{d_jobs, njobs, ctas, ncy, nmr, exec, gc.tick});
+    ++gc.captures;
+    *out = exec;
+    return QXD_OK;
+}
+
+}  // namespace
+
+int sap_apply_batch(std::vector<SapJob>& jobs, SapJob* d_jobs, int ncy, int nmr, cudaStream_t st,
+                    SapGraphCache* graphs) {
     if (jobs.empty()) return QXD_OK;
     int ctas = 0;
-    for (auto& J : jobs) {
+    for (auto& J : jobs) {  // psi = 0 is set by the first launch itself
         J.cta_begin = ctas;
         ctas += J.sg.nhalf;
-        QXD_CUDA(cudaMemsetAsync((void*)J.f.psi, 0, (size_t)J.g.V * 24 * sizeof(float), st));
     }
     QXD_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(SapJob), cudaMemcpyHostToDevice, st));
     const size_t smem = sap_smem_bytes<float>();
     int rc = split_attrs(k_sap_block_batch, smem);
     if (rc) return rc;
-    for (int cy = 0; cy < ncy; ++cy)
-        for (int colour = 0; colour < 2; ++colour) {
-            const int psi_zero = (cy == 0 && colour == 0) ? 1 : 0;
-            k_sap_block_batch<<<ctas, SPLIT_THREADS, smem, st>>>(d_jobs, (int)jobs.size(), colour, psi_zero, nmr);
-            QXD_LAUNCHED("k_sap_block_batch");
-        }
+    const int njobs = (int)jobs.size();
+    if (graphs) {
+        cudaGraphExec_t exec = nullptr;
+        if ((rc = batch_graph(*graphs, d_jobs, njobs, ctas, ncy, nmr, smem, &exec))) return rc;
+        QXD_CUDA(cudaGraphLaunch(exec, st));
+        return QXD_OK;
+    }
+    launch_batch_set(d_jobs, njobs, ctas, ncy, nmr, smem, st);
+    QXD_LAUNCHED("k_sap_block_batch");
     return QXD_OK;
 }
 template int sap_apply<double>(qxd_lattice*, SapWork&, void*, const void*, int, int, cudaStream_t);

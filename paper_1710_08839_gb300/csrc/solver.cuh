@@ -33,9 +33,33 @@ struct SapJob {
     int cta_begin;
 };
 SapGeom sap_geom(const Geom& g);
+
+// CUDA graphs of the batched Schwarz launch set. For a given job table, job
+// count, CTA count, ncy and nmr the 2 ncy launches of one application have
+// fixed arguments (the table contents are copied in before each replay), so
+// the set is captured once on a private stream and replayed with one graph
+// launch. At most kMax graphs are kept, the least recently used is dropped.
+struct SapGraphCache {
+    static constexpr int kMax = 16;
+    struct Entry {
+        const void* table;
+        int njobs, ctas, ncy, nmr;
+        cudaGraphExec_t exec;
+        unsigned long long last;
+    };
+    std::vector<Entry> entries;
+    cudaStream_t cap = nullptr;
+    unsigned long long tick = 0;
+    long long captures = 0, replays = 0;
+    void clear();    // destroys the graphs (those in flight finish first)
+    void release();  // clear() and the capture stream
+};
+
 // every job's SAP in one launch per half-cycle; d_jobs: device table with
-// room for jobs.size() entries
-int sap_apply_batch(std::vector<SapJob>& jobs, SapJob* d_jobs, int ncy, int nmr, cudaStream_t st);
+// room for jobs.size() entries; graphs: replay the launch set from this
+// cache (nullptr: plain launches)
+int sap_apply_batch(std::vector<SapJob>& jobs, SapJob* d_jobs, int ncy, int nmr, cudaStream_t st,
+                    SapGraphCache* graphs = nullptr);
 
 struct SolverWork {
     int V = 0, nkv = 0, prec = -1;

@@ -118,6 +118,7 @@ SIGNATURES = {
     "qxd_engine_run": (_i, [_vp]),
     "qxd_engine_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
                               ctypes.POINTER(ctypes.c_longlong)]),
+    "qxd_engine_graph_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "qxd_sw_logdet": (_i, [_vp, _i, ctypes.POINTER(_d)]),
     "qxd_mscg_defaults": (None, [ctypes.POINTER(qxd_mscg_params)]),
     "qxd_mscg": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_vp), _vp, ctypes.POINTER(qxd_mscg_params),
@@ -560,6 +561,12 @@ class Engine:
         a, h, s = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_longlong()
         check(_call("qxd_engine_stats", self.handle, ctypes.byref(a), ctypes.byref(h), ctypes.byref(s)))
         return {"bytes_in_use": a.value, "bytes_held": h.value, "steps": s.value}
+
+    def graph_stats(self):
+        """Captures and replays of the CUDA graphs of batched SAP launch sets."""
+        c, r = ctypes.c_longlong(), ctypes.c_longlong()
+        check(_call("qxd_engine_graph_stats", self.handle, ctypes.byref(c), ctypes.byref(r)))
+        return {"captures": c.value, "replays": r.value}
 
     def close(self):
         if self.handle:

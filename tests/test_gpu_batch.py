@@ -136,6 +136,10 @@ def test_engine_results_same_alone_and_in_mix():
         assert done and info["status"] == qxd.QXD_OK, info
         assert info["true_relres"] <= 1e-10
         infos.append(info)
+    # the batched SAP launch set is captured once per job mix and replayed
+    gs = eng.graph_stats()
+    assert gs["captures"] >= 1 and gs["replays"] >= 1, gs
+    assert gs["captures"] + gs["replays"] <= eng.stats()["steps"], gs
     eng.close()
     # each alone, in a fresh engine
     for (c, v, b), xm in zip(reqs, xs_mix):
