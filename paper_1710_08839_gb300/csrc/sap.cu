@@ -12,8 +12,11 @@
 //         even-odd form D_hat_B = M_ee - H_eo M_oo^-1 H_oe of the block
 //   psi_B += delta
 // Starting from psi = 0, ncy cycles give psi = SAP(eta).
-// The block spinors live in shared memory; links and clover blocks are read
-// from the global fields.
+// FP32 (k_sap_split, k_sap_block_batch): two threads per site pair, the
+// block's interior links and three block fields in shared memory, the clover
+// blocks read through L1. FP64 (k_sap_block): one thread per site pair, the
+// block fields in shared memory, links and clover blocks from the global
+// fields.
 #include <algorithm>
 #include <vector>
 
@@ -25,7 +28,6 @@ namespace qxd {
 namespace {
 
 constexpr int SAP_BS = 4;          // block extent in every direction
-constexpr int SAP_SITES = 256;     // sites per block
 constexpr int SAP_HALF = 128;      // sites of one parity per block
 constexpr int SAP_THREADS = 128;   // one thread per (even, odd) site pair
 
@@ -46,41 +48,13 @@ struct SmemField {
     }
 };
 
-// Links of the block: FP32 keeps them in shared memory (two rows + angle,
-// 53 KB per block), loaded once per block visit; FP64 reads the global field.
+// Links of the block for the one-thread-per-pair form (FP64): read from the
+// global field.
 template <typename R>
 struct BlockLinks;
 
 template <>
-struct BlockLinks<float> {
-    static constexpr bool kStaged = true;
-    float4* U;   // [4][3][256] by local site index
-    float2* Z;   // [4][256] z^qhat = exp(i qhat A), computed once per block visit
-    __device__ __forceinline__ void link(const Fields<float>&, const Geom&, int mu, int lidx, int,
-                                         cplx<float> u[3][3]) const {
-        const float4 a = U[(mu * 3 + 0) * SAP_SITES + lidx];
-        const float4 b = U[(mu * 3 + 1) * SAP_SITES + lidx];
-        const float4 c = U[(mu * 3 + 2) * SAP_SITES + lidx];
-        u[0][0] = mk(a.x, a.y);
-        u[0][1] = mk(a.z, a.w);
-        u[0][2] = mk(b.x, b.y);
-        u[1][0] = mk(b.z, b.w);
-        u[1][1] = mk(c.x, c.y);
-        u[1][2] = mk(c.z, c.w);
-        u[2][0] = conj(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
-        u[2][1] = conj(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
-        u[2][2] = conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
-    }
-    __device__ __forceinline__ cplx<float> phase(const Fields<float>&, const Geom&, int mu, int lidx, int,
-                                                 float) const {
-        const float2 z = Z[mu * SAP_SITES + lidx];
-        return mk(z.x, z.y);
-    }
-};
-
-template <>
 struct BlockLinks<double> {
-    static constexpr bool kStaged = false;
     __device__ __forceinline__ void link(const Fields<double>& f, const Geom& g, int mu, int, int s,
                                          cplx<double> u[3][3]) const {
         load_link(f.U, g.V, mu, s, u);
@@ -143,7 +117,7 @@ __device__ __forceinline__ void block_dir(const Geom& g, const Fields<R>& f, con
     if (t.l[MU] > 0) {
         src.load((t.lidx - stride) >> 1, v);
         project<R, MU, -1>(v, h0, h1);
-        const int sb = BlockLinks<R>::kStaged ? 0 : back_native<MU>(g, t);
+        const int sb = back_native<MU>(g, t);
         bl.link(f, g, MU, t.lidx - stride, sb, u);
         su3_dag_mul(u, h0, g0);
         su3_dag_mul(u, h1, g1);
@@ -223,11 +197,6 @@ __device__ __forceinline__ void block_sum3(R a, R b, R c, R* red, R out[3]) {
     if (TAIL_SYNC) __syncthreads();
 }
 
-template <typename R>
-constexpr size_t sap_link_bytes() {
-    return BlockLinks<R>::kStaged ? (12 * SAP_SITES * sizeof(float4) + 4 * SAP_SITES * sizeof(float2)) : 0;
-}
-
 // Each thread owns one even and one odd site of the block: the local pair
 // (2t, 2t + 1). Phases in order (each block-hop phase is one call of
 // block_hops from a single call site, which keeps the code small):
@@ -243,13 +212,7 @@ __device__ __forceinline__ void sap_block_body(const Geom& g, const SapGeom& sg,
                                                const typename Fields<R>::vec* __restrict__ eta, int nmr, R q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BlockLinks<R> bl;
-    unsigned char* sp = smem_raw;
-    if constexpr (BlockLinks<R>::kStaged) {
-        bl.U = reinterpret_cast<float4*>(sp);
-        bl.Z = reinterpret_cast<float2*>(sp + 12 * SAP_SITES * sizeof(float4));
-        sp += sap_link_bytes<R>();
-    }
-    R* sm = reinterpret_cast<R*>(sp);
+    R* sm = reinterpret_cast<R*>(smem_raw);
     const SmemField<R> s_ro{sm};                    // r on the odd sites
     const SmemField<R> s_rho{sm + 24 * SAP_HALF};   // MR residual (even)
     const SmemField<R> s_t{sm + 48 * SAP_HALF};     // odd temporary / delta_e at the end
@@ -276,25 +239,6 @@ __device__ __forceinline__ void sap_block_body(const Geom& g, const SapGeom& sg,
     const int par0 = ((base >> 6) + ((base >> 4) & 3) + ((base >> 2) & 3) + (base & 3)) & 1;
     const Site se = make_site(g, org, base + par0);
     const Site so = make_site(g, org, base + 1 - par0);
-
-    if constexpr (BlockLinks<R>::kStaged) {
-        // links and angles of the block's sites, all four directions
-#pragma unroll 1
-        for (int k = 0; k < 2; ++k) {
-            const Site& st_ = k ? so : se;
-#pragma unroll
-            for (int mu = 0; mu < 4; ++mu) {
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    bl.U[(mu * 3 + j) * SAP_SITES + st_.lidx] = f.U[((size_t)mu * 3 + j) * g.V + st_.s];
-            }
-#pragma unroll
-            for (int mu = 0; mu < 4; ++mu) {
-                const cplx<float> z = QNZ ? link_phase(f.A, g.V, mu, st_.s, q) : mk(1.f, 0.f);
-                bl.Z[mu * SAP_SITES + st_.lidx] = make_float2(z.re, z.im);
-            }
-        }
-    }
 
     // residual r = eta - D psi on both sites (one call site)
     cplx<R> re[12], v[12], w[12], acc[12];
@@ -787,7 +731,7 @@ template <typename R>
 size_t sap_smem_bytes() {
     if (sizeof(R) == 4)  // split kernel: interior links, three block fields, reduction slots of 8 warps
         return split_link_bytes() + (72 * SAP_HALF + 3 * (SPLIT_THREADS / 32)) * sizeof(R);
-    return sap_link_bytes<R>() + (72 * SAP_HALF + 3 * (SAP_THREADS / 32)) * sizeof(R);
+    return (72 * SAP_HALF + 3 * (SAP_THREADS / 32)) * sizeof(R);
 }
 
 // Dynamic shared memory of the split kernel, and an L1/shared carveout just
