@@ -339,7 +339,8 @@ __global__ void __launch_bounds__(SAP_THREADS, 2) k_sap_block(Geom g, SapGeom sg
 // (mu = 1, 2). The partner's share is exchanged once per hop set with a warp
 // shuffle. The clover term acts within a chirality, so each thread computes
 // its three rows of both 6x6 blocks after one shuffle of the partner's half.
-// The arithmetic per block is that of the one-thread-per-pair form, spread
+// The arithmetic per block is that of the one-thread-per-pair form, except
+// that both threads of a pair rebuild each link's third row; it is spread
 // over twice the threads at about half the registers each.
 // ---------------------------------------------------------------------------
 constexpr int SPLIT_THREADS = 256;
