@@ -76,3 +76,15 @@ def test_pseudofermion_entry_points_check_arguments():
     assert info.status == qxd.QXD_ERR_ARG
     assert lib.qxd_rational_apply(None, 1, sig, sig, None, None, ctypes.byref(p), ctypes.byref(info),
                                   None) == qxd.QXD_ERR_ARG
+
+
+def test_engine_entry_points_check_arguments():
+    lib = qxd.lib()
+    c, r = ctypes.c_longlong(), ctypes.c_longlong()
+    assert lib.qxd_engine_graph_stats(None, ctypes.byref(c), ctypes.byref(r)) == qxd.QXD_ERR_ARG
+    a, h, s = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_longlong()
+    assert lib.qxd_engine_stats(None, ctypes.byref(a), ctypes.byref(h), ctypes.byref(s)) == qxd.QXD_ERR_ARG
+    assert lib.qxd_engine_create(None, 0, 1, None) == qxd.QXD_ERR_ARG
+    e = ctypes.c_void_p()
+    assert lib.qxd_engine_create(ctypes.byref(e), 0, 0, None) == qxd.QXD_ERR_ARG
+    assert lib.qxd_engine_destroy(None) == qxd.QXD_OK
