@@ -559,6 +559,38 @@ def gcr(apply, b, tol: float = 1e-13, nkv: int = 16, max_iter: int = 20000, x0=N
 # ---------------------------------------------------------------------------
 
 
+def block_mr(A, c, block_id, nblocks: int, nmr: int, mask):
+    """nmr minimal-residual steps on A y = c from y = 0, rho = c, on every
+    block at once (A maps fields supported on `mask` to such fields and does
+    not couple blocks). Step: w = A rho, omega_b = <w, rho>_b / <w, w>_b with
+    the inner products summed over block b (omega_b = 0 where w vanishes on
+    b), y += omega rho, rho -= omega w. That omega minimises the block norm
+    of rho - omega w, so the new rho is orthogonal to w on every block, and
+    rho = c - A y throughout. Returns (y, rho). This is the block solve of
+    the Schwarz method below, which the paper names without giving it."""
+    y = np.zeros_like(c)
+    rho = c.copy()
+
+    def restrict(f):
+        g = np.zeros_like(f)
+        g[mask] = f[mask]
+        return g
+
+    for _ in range(nmr):
+        w = A(rho)
+        wr = np.einsum("nsc,nsc->n", np.conj(w), rho)
+        ww = np.einsum("nsc,nsc->n", np.conj(w), w).real
+        num = np.bincount(block_id, weights=wr.real, minlength=nblocks) + \
+            1j * np.bincount(block_id, weights=wr.imag, minlength=nblocks)
+        den = np.bincount(block_id, weights=ww, minlength=nblocks)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            om = np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)
+        omega = om[block_id][:, None, None]
+        y = restrict(y + omega * rho)
+        rho = restrict(rho - omega * w)
+    return y, rho
+
+
 def sap(op: Dirac, eta, ncy: int, nmr: int, bs: int = 4):
     """SAP(eta): multiplicative Schwarz method on bs^4 blocks.
 
@@ -567,15 +599,12 @@ def sap(op: Dirac, eta, ncy: int, nmr: int, bs: int = 4):
     the parity of their block coordinates. Starting from psi = 0, each of the
     ncy cycles visits colour 0, then colour 1. For the blocks B of a colour:
       r = eta - D psi                                  (whole lattice)
-      delta_B ~ D_B^-1 r_B by nmr minimal-residual steps on the even-odd
-               form D_hat_B = D_ee - D_eo D_oo^-1 D_oe of D_B
+      delta_B ~ D_B^-1 r_B by nmr minimal-residual steps (block_mr) on the
+               even-odd form D_hat_B = D_ee - D_eo D_oo^-1 D_oe of D_B
       psi_B += delta_B
     where D_B is D restricted to B with the hops leaving B dropped. Blocks of
     one colour never touch, so D restricted to all of them is the direct sum
     of their D_B, and all of them are handled at once here.
-    Minimal-residual step on A y = c from y = 0, rho = c:
-      w = A rho, omega = <w, rho> / <w, w>, y += omega rho, rho -= omega w,
-    with the inner products taken per block.
     """
     lat = op.lat
     V = lat.V
@@ -630,20 +659,7 @@ def sap(op: Dirac, eta, ncy: int, nmr: int, bs: int = 4):
             r = restrict(eta - op.apply(psi), inb)
             # even-odd source: c_e = r_e - D_eo D_oo^-1 r_o
             ce = restrict(r, even_b) - D_B_eo(Doo_inv_B(r), even_b, odd_b)
-            y = np.zeros_like(ce)
-            rho = ce.copy()
-            for _ in range(nmr):
-                w = D_hat_B(rho)
-                wr = np.einsum("nsc,nsc->n", np.conj(w), rho)
-                ww = np.einsum("nsc,nsc->n", np.conj(w), w).real
-                num = np.bincount(block_id, weights=wr.real, minlength=np.prod(nb)) + \
-                    1j * np.bincount(block_id, weights=wr.imag, minlength=np.prod(nb))
-                den = np.bincount(block_id, weights=ww, minlength=np.prod(nb))
-                with np.errstate(invalid="ignore", divide="ignore"):
-                    om = np.where(den > 0, num / np.where(den > 0, den, 1.0), 0.0)
-                omega = om[block_id][:, None, None]
-                y = restrict(y + omega * rho, even_b)
-                rho = restrict(rho - omega * w, even_b)
+            y, _ = block_mr(D_hat_B, ce, block_id, int(np.prod(nb)), nmr, even_b)
             # odd part: y_o = D_oo^-1 (r_o - D_oe y_e)
             yo = Doo_inv_B(restrict(r, odd_b) - D_B_eo(y, odd_b, even_b))
             psi = psi + y + yo

@@ -11,6 +11,8 @@ The block size is a parameter of the oracle; these pins use 2^4 blocks on a
 512-site C* lattice so that they run in seconds (the GPU comparisons use the
 4^4 blocks of the library).
 """
+import inspect
+
 import numpy as np
 import pytest
 
@@ -84,3 +86,124 @@ def test_planted_wrong_block_inverse_is_caught(monkeypatch):
                                                             (len(sites), 12, 12)).copy())
     r1, _ = last_colour_residual(op, eta, lat, nmr=60)
     assert r1 > 1e-6
+
+
+# Plausible mistakes planted in a copy of the oracle's sap (one line each).
+# Every one must fail at least one of the pins above: a pin that cannot fail
+# pins nothing.
+PLANTED = {
+    "sign of the odd-site reconstruction": ("yo = Doo_inv_B(restrict(r, odd_b) - D_B_eo(y, odd_b, even_b))",
+                                            "yo = Doo_inv_B(restrict(r, odd_b) + D_B_eo(y, odd_b, even_b))"),
+    "sign of the even-odd source": ("ce = restrict(r, even_b) - D_B_eo(Doo_inv_B(r), even_b, odd_b)",
+                                    "ce = restrict(r, even_b) + D_B_eo(Doo_inv_B(r), even_b, odd_b)"),
+    "sign of the Schur complement": ("return D_B_eo(f, even_b, even_b) - D_B_eo(",
+                                     "return D_B_eo(f, even_b, even_b) + D_B_eo("),
+    "residual not updated after the first colour": ("r = restrict(eta - op.apply(psi), inb)",
+                                                    "r = restrict(eta, inb)"),
+    "one colour visited twice": ("for col in (0, 1):", "for col in (0, 0):"),
+}
+
+
+def planted_sap(old, new):
+    src = inspect.getsource(O.qxd_oracle.sap)
+    assert src.count(old) == 1, old
+    ns = dict(vars(O.qxd_oracle))
+    exec(compile(src.replace(old, new), "<planted sap>", "exec"), ns)
+    return ns["sap"]
+
+
+def pins_hold(sap):
+    """The three pins above, for a given implementation of SAP."""
+    lat, op, eta = setup()
+    col = colour_of(lat)
+    n = np.linalg.norm(eta)
+    p1 = sap(op, eta, ncy=1, nmr=60, bs=BS)
+    r = eta - op.apply(p1)
+    if not (np.linalg.norm(r[col == 1]) / n < 1e-10 and np.linalg.norm(r[col == 0]) / n > 1e-3):
+        return False
+    a = 0.7 - 1.3j
+    p2 = sap(op, a * eta, ncy=1, nmr=60, bs=BS)
+    if not np.abs(p2 - a * p1).max() / np.abs(p2).max() < 1e-10:
+        return False
+    res = [np.linalg.norm(eta - op.apply(sap(op, eta, ncy=k, nmr=20, bs=BS))) / n for k in (1, 2, 4)]
+    return all(b < 0.7 * a for a, b in zip(res, res[1:])) and res[-1] < 2e-2
+
+
+@pytest.mark.parametrize("name", list(PLANTED))
+def test_planted_sap_mistakes_are_caught(name):
+    assert not pins_hold(planted_sap(*PLANTED[name])), name
+
+
+# The block solve itself (nmr minimal-residual steps). Its defining
+# properties: rho = c - A y after every step, and each step's omega minimises
+# the block norm of rho - omega w, i.e. the new rho is orthogonal to w = A rho
+# on every block (so the block residual never grows). Checked on a random
+# non-Hermitian block-diagonal operator with a masked support.
+
+def mr_problem(seed=4):
+    rng = np.random.default_rng(seed)
+    nb, per = 3, 8                              # 3 blocks of 8 sites
+    V = nb * per
+    block_id = np.arange(V) // per
+    mask = (np.arange(V) % 2) == 0              # the operator lives on half the sites
+    idx = [np.flatnonzero((block_id == b) & mask) for b in range(nb)]
+    mats = [np.eye(12 * len(i)) + 0.3 * (rng.normal(size=(12 * len(i),) * 2)
+                                         + 1j * rng.normal(size=(12 * len(i),) * 2)) / np.sqrt(12 * len(i))
+            for i in idx]
+
+    def A(f):
+        g = np.zeros_like(f)
+        for i, m in zip(idx, mats):
+            g[i] = (m @ f[i].reshape(-1)).reshape(len(i), 4, 3)
+        return g
+
+    c = np.zeros((V, 4, 3), dtype=complex)
+    c[mask] = rng.normal(size=(mask.sum(), 4, 3)) + 1j * rng.normal(size=(mask.sum(), 4, 3))
+    return A, c, block_id, nb, mask
+
+
+def mr_pins_hold(block_mr):
+    A, c, block_id, nb, mask = mr_problem()
+    prev = None
+    for k in range(5):
+        y, rho = block_mr(A, c, block_id, nb, k, mask)
+        if np.linalg.norm(c - A(y) - rho) > 1e-12 * np.linalg.norm(c):
+            return False
+        if np.count_nonzero(y[~mask]) or np.count_nonzero(rho[~mask]):
+            return False
+        if prev is not None:
+            w = A(prev)
+            for b in range(nb):
+                sel = block_id == b
+                overlap = abs(np.vdot(w[sel], rho[sel]))
+                if overlap > 1e-12 * np.linalg.norm(w[sel]) * np.linalg.norm(prev[sel]):
+                    return False
+                if np.linalg.norm(rho[sel]) > np.linalg.norm(prev[sel]) * (1 + 1e-14):
+                    return False
+        prev = rho
+    return np.linalg.norm(prev) < 0.9 * np.linalg.norm(c)
+
+
+def test_block_minimal_residual_steps():
+    assert mr_pins_hold(O.block_mr)
+
+
+PLANTED_MR = {
+    "conjugated step length": ('wr = np.einsum("nsc,nsc->n", np.conj(w), rho)',
+                               'wr = np.einsum("nsc,nsc->n", w, np.conj(rho))'),
+    "one omega for all blocks": ("omega = om[block_id][:, None, None]",
+                                 "omega = num.sum() / max(den.sum(), 1e-300)"),
+    "solution updated along w": ("y = restrict(y + omega * rho)", "y = restrict(y + omega * w)"),
+    "step length without the conjugate of w": ('wr = np.einsum("nsc,nsc->n", np.conj(w), rho)',
+                                               'wr = np.einsum("nsc,nsc->n", w, rho)'),
+}
+
+
+@pytest.mark.parametrize("name", list(PLANTED_MR))
+def test_planted_mr_mistakes_are_caught(name):
+    old, new = PLANTED_MR[name]
+    src = inspect.getsource(O.qxd_oracle.block_mr)
+    assert src.count(old) == 1, old
+    ns = dict(vars(O.qxd_oracle))
+    exec(compile(src.replace(old, new), "<planted block_mr>", "exec"), ns)
+    assert not mr_pins_hold(ns["block_mr"]), name
