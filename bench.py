@@ -27,7 +27,8 @@ import subprocess
 import sys
 import time
 
-# the CPU baseline is the plain oracle on one core: keep host BLAS single-threaded
+# the oracle runs one process per core (or on one core): keep host BLAS
+# single-threaded in every process
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
@@ -109,7 +110,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "25"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -140,7 +141,7 @@ class ClockSampler:
                 ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
             except ValueError:
                 ts = None
-            if t0 is not None and ts is not None and not (t0 - 0.15 <= ts <= t1 + 0.15):
+            if t0 is not None and ts is not None and not (t0 - 0.05 <= ts <= t1 + 0.05):
                 continue
             f = f[1:]
             try:
@@ -776,6 +777,29 @@ def dfl_benchmark(qxd, torch):
     return out
 
 
+def alu_benchmark(qxd, torch):
+    """FP64 and FP32 fused multiply-add throughput of this GPU (qxd_fma_rate):
+    the denominators of the ALU-bound rooflines, with the SM clock seen."""
+    props = torch.cuda.get_device_properties(0)
+    kinds = (("fp64_fma", qxd.QXD_PROBE_FMA64, 5000), ("fp32_fma", qxd.QXD_PROBE_FMA32, 400000),
+             ("fp32x2_fma", qxd.QXD_PROBE_FMA32X2, 200000))
+    out = {"gpu": props.name, "sms": props.multi_processor_count,
+           "probe": "16 independent FMA chains per thread, 8 blocks of 256 threads per SM, "
+                    "best of 3 launches (CUDA events); 2 flops per FMA"}
+    for name, kind, iters in kinds:
+        qxd.fma_rate(kind, max(1, iters // 10))  # clocks up, module loaded
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            t0 = time.time()
+            rate = qxd.fma_rate(kind, iters)
+            t1 = time.time()
+        c = clk.summary(t0, t1)
+        row = {"TFLOP/s": rate / 1e12, "clocks": c}
+        if c.get("sm_mhz"):
+            row["flop_per_clk_per_sm"] = rate / (props.multi_processor_count * c["sm_mhz"] * 1e6)
+        out[name] = row
+    return out
+
+
 def sap_benchmark(qxd, torch, steps, w):
     """Time one FP32 SAP application (ncy 5, nmr 5) on the lattice of workload w."""
     su3, ang, psi, V = make_inputs("cuda", w)
@@ -801,6 +825,102 @@ def sap_benchmark(qxd, torch, steps, w):
             "lattice": f"{w['T']}x{2 * w['L1']}x{w['L2']}x{w['L3']}"}
 
 
+# --- the oracle on all host cores ------------------------------------------
+# The oracle is plain numpy; its many small array operations hold the GIL, so
+# threads do not scale. All cores are used by a process pool started with
+# "spawn" (a fresh interpreter: no CUDA state is inherited). The workers map
+# the gauge field and the spinor read-only from .npy files written once to
+# /dev/shm (or to a temporary directory when /dev/shm is too small).
+
+_W_OP = None
+_W_PSI = None
+
+
+def _oracle_worker_init(paths, w):
+    global _W_OP, _W_PSI
+    import numpy as np
+
+    import oracle as O
+    su3 = np.load(paths["su3"], mmap_mode="r")
+    ang = np.load(paths["ang"], mmap_mode="r")
+    _W_PSI = np.load(paths["psi"], mmap_mode="r")
+    lat = O.Lattice(w["T"], w["L1"], w["L2"], w["L3"], w["mask"])
+    _W_OP = O.Dirac(lat, O.GaugeField.from_physical(lat, su3, ang), w["m0"], w["csw"], w["cswqed"], w["qhat"])
+
+
+def _oracle_worker_apply(idx):
+    _W_OP.apply_at(_W_PSI, idx)
+    return len(idx)
+
+
+class OraclePool:
+    """The FP64 oracle's D on sampled sites of a workload, on `nproc` processes."""
+
+    def __init__(self, su3_host, ang_host, psi_host, w, nproc=None):
+        import multiprocessing as mp
+        import shutil
+        import tempfile
+
+        import numpy as np
+        self.nproc = nproc or len(os.sched_getaffinity(0))
+        need = su3_host.nbytes + ang_host.nbytes + psi_host.nbytes + (1 << 28)
+        base = None
+        for d in ("/dev/shm", tempfile.gettempdir()):
+            try:
+                if os.path.isdir(d) and shutil.disk_usage(d).free > need:
+                    base = d
+                    break
+            except OSError:
+                continue
+        if base is None:
+            raise RuntimeError("no room to share the fields with the oracle's worker processes")
+        self.dir = tempfile.mkdtemp(prefix="qxd_oracle_", dir=base)
+        try:
+            self.paths = {}
+            for k, a in (("su3", su3_host), ("ang", ang_host), ("psi", psi_host)):
+                self.paths[k] = os.path.join(self.dir, k + ".npy")
+                np.save(self.paths[k], np.ascontiguousarray(a))
+            ctx = mp.get_context("spawn")
+            self.pool = ctx.Pool(self.nproc, initializer=_oracle_worker_init, initargs=(self.paths, dict(w)))
+        except BaseException:
+            shutil.rmtree(self.dir, ignore_errors=True)
+            raise
+        self.where = base
+
+    def apply(self, idx):
+        """Wall seconds of the oracle's D at sites idx, split over the workers."""
+        import numpy as np
+        parts = [p for p in np.array_split(np.asarray(idx), 4 * self.nproc) if len(p)]
+        t0 = time.perf_counter()
+        n = sum(self.pool.map(_oracle_worker_apply, parts, chunksize=1))
+        dt = time.perf_counter() - t0
+        assert n == len(idx)
+        return dt
+
+    def close(self):
+        import shutil
+        self.pool.close()
+        self.pool.join()
+        shutil.rmtree(self.dir, ignore_errors=True)
+
+
+def oracle_sample_rate_all_cores(su3_host, ang_host, psi_host, V, w, target_s=15.0):
+    """FP64 oracle on a sample of sites on all host cores: (sites/s, sites, seconds, cores)."""
+    import numpy as np
+    pool = OraclePool(su3_host, ang_host, psi_host, w)
+    try:
+        rng = np.random.default_rng(8)
+        n = 2048 * pool.nproc
+        pool.apply(rng.choice(V, size=n, replace=False))          # workers start, pages mapped
+        dt = pool.apply(rng.choice(V, size=n, replace=False))
+        n2 = int(min(4_000_000, max(n, n * target_s / max(dt, 1e-3))))
+        idx = rng.choice(V, size=n2, replace=False)
+        dt = pool.apply(idx)
+        return n2 / dt, n2, dt, pool.nproc
+    finally:
+        pool.close()
+
+
 def oracle_sample_rate(su3_host, ang_host, psi_host, V, w, target_s=12.0):
     """FP64 oracle on a sample of sites of the workload: (sites/s, sites, seconds)."""
     import numpy as np
@@ -824,7 +944,8 @@ def oracle_sample_rate(su3_host, ang_host, psi_host, V, w, target_s=12.0):
 
 
 def run_reference(args):
-    """The reference arm: the FP64 oracle on the host cores, sampled steps."""
+    """The reference arm: the FP64 oracle on the host cores (one process per
+    core), on a bounded random sample of sites of the workload per step."""
     import numpy as np
     import torch
 
@@ -837,23 +958,36 @@ def run_reference(args):
     su3h, angh, psih = su3.cpu().numpy(), ang.cpu().numpy(), psi.numpy()
     del su3, ang
     w = WORKLOAD
-    lat = O.Lattice(w["T"], w["L1"], w["L2"], w["L3"], w["mask"])
-    op = O.Dirac(lat, O.GaugeField.from_physical(lat, su3h, angh), w["m0"], w["csw"],
-                 w["cswqed"], w["qhat"])
     rng = np.random.default_rng(11)
+    try:
+        pool = OraclePool(su3h, angh, psih, w)
+        cores = pool.nproc
+        run = pool.apply
+        how = f"{cores} processes, one per host core"
+    except Exception as e:  # no room to share the fields: one core in this process
+        pool, cores = None, 1
+        lat = O.Lattice(w["T"], w["L1"], w["L2"], w["L3"], w["mask"])
+        op = O.Dirac(lat, O.GaugeField.from_physical(lat, su3h, angh), w["m0"], w["csw"],
+                     w["cswqed"], w["qhat"])
+
+        def run(idx):
+            t0 = time.perf_counter()
+            op.apply_at(psih, idx)
+            return time.perf_counter() - t0
+        how = f"one core (all-cores run unavailable: {e})"
     # size each step so that warm-up + timed steps take about 90 s in total
-    cal = rng.choice(V, size=512, replace=False)
-    t0 = time.perf_counter()
-    op.apply_at(psih, cal)
-    rate = 512 / (time.perf_counter() - t0)
-    S = int(min(8192, max(64, rate * 90.0 / (args.steps + args.warmup))))
+    cal = 512 * cores
+    run(rng.choice(V, size=cal, replace=False))
+    rate = cal / run(rng.choice(V, size=cal, replace=False))
+    S = int(min(8192 * cores, max(64 * cores, rate * 90.0 / (args.steps + args.warmup))))
     samples = [rng.choice(V, size=S, replace=False) for _ in range(args.warmup + args.steps)]
     for i in range(args.warmup):
-        op.apply_at(psih, samples[i])
-    t0 = time.perf_counter()
+        run(samples[i])
+    dt = 0.0
     for i in range(args.steps):
-        op.apply_at(psih, samples[args.warmup + i])
-    dt = time.perf_counter() - t0
+        dt += run(samples[args.warmup + i])
+    if pool:
+        pool.close()
     sites_s = S * args.steps / dt
     # the metric's byte model (688 B per site), so the ratio of the two arms
     # is the ratio of sites per second
@@ -867,9 +1001,9 @@ def run_reference(args):
         "config": {"workload": "Dw apply FP32 (2-row SU(3) + U(1) angle), doubled 96x96x48x48 "
                                "C* lattice (L=48, T=96), qhat=2, csw=cswqed=1",
                    "sites": V, "bytes_per_site": b,
-                   "sample": f"FP64 oracle at {S} random sites per step (one core)"},
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{S} random sites per step x {args.steps} steps "
+                   "sample": f"FP64 oracle at {S} random sites per step ({how})"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{S} random sites per step x {args.steps} steps on {how} "
                                    f"({sites_s:.0f} sites/s)"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -886,12 +1020,16 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
-    ap.add_argument("--mode", default="dw", choices=["dw", "solve", "sap", "batch", "serve", "rational", "flow", "dfl"],
+    ap.add_argument("--mode", default="dw",
+                    choices=["dw", "solve", "sap", "batch", "serve", "rational", "flow", "dfl", "alu"],
                     help="dw: the Dw throughput line (plus a solver summary unless --no-solve); "
                          "solve: solver comparison only; sap: time the SAP preconditioner only; "
                          "batch / serve: multi-RHS and serving workloads; rational: pseudofermion action; "
-                         "flow: Wilson flow and gauge observables; dfl: deflated vs SAP solver")
+                         "flow: Wilson flow and gauge observables; dfl: deflated vs SAP solver; "
+                         "alu: FP64/FP32 FMA throughput (the ALU roofline denominators)")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the multi-RHS summary of the default line")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving summary of the default line")
     ap.add_argument("--write-traffic", metavar="NCU_CSV",
                     help="write profiles/dirac_fp32_q2_traffic.json from an ncu CSV of k_dirac launches and exit")
     args = ap.parse_args()
@@ -914,8 +1052,10 @@ def main():
     ge.build()
     from paper_1710_08839_gb300 import qxd
 
-    if args.mode in ("solve", "sap", "batch", "serve", "rational", "flow", "dfl"):
-        if args.mode == "dfl":
+    if args.mode in ("solve", "sap", "batch", "serve", "rational", "flow", "dfl", "alu"):
+        if args.mode == "alu":
+            res = alu_benchmark(qxd, torch)
+        elif args.mode == "dfl":
             res = dfl_benchmark(qxd, torch)
         elif args.mode == "flow":
             res = flow_benchmark(qxd, torch)
@@ -1020,21 +1160,38 @@ def main():
                "h2d_bytes_per_step": V * 96, "d2h_bytes_per_step": V * 96, "ms_per_step": e2e_ms}
         del xh, yh
 
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and not args.no_cpu_baseline:
         su3h, angh = su3.cpu().numpy(), ang.cpu().numpy()
-        rate, n, dt = oracle_sample_rate(su3h, angh, psi.numpy(), V, w)
-        cpu = {"value": rate * bps / 1e9, "unit": "GB/s", "cores": 1,
-               "kind": "oracle",
-               "sample": f"FP64 oracle D at {n} random sites of the workload in {dt:.1f} s "
-                         f"({rate:.0f} sites/s x {bps} B/site, the metric's byte model)"}
+        rate, n, dt = oracle_sample_rate(su3h, angh, psi.numpy(), V, w, target_s=8.0)
+        cpu1 = {"value": rate * bps / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                "sample": f"FP64 oracle D at {n} random sites of the workload in {dt:.1f} s on one core "
+                          f"({rate:.0f} sites/s x {bps} B/site, the metric's byte model)"}
+        try:
+            rate, n, dt, cores = oracle_sample_rate_all_cores(su3h, angh, psi.numpy(), V, w)
+            cpu = {"value": rate * bps / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                   "sample": f"FP64 oracle D at {n} random sites of the workload in {dt:.1f} s on "
+                             f"{cores} processes, one per host core ({rate:.0f} sites/s x {bps} B/site, "
+                             "the metric's byte model)"}
+        except Exception as e:  # no room to share the fields: the one-core figure stands
+            cpu = dict(cpu1, note=f"all-cores run unavailable: {e}")
+        del su3h, angh
 
-    solve = None
-    if not args.no_solve:
+    solve = batch = serve = None
+    if not (args.no_solve and args.no_batch and args.no_serve):
         lat.close()
         xn = yn = None
+        del su3, ang
         torch.cuda.empty_cache()
+    if not args.no_solve:
         solve = solve_benchmark(qxd, torch)
+        torch.cuda.empty_cache()
+    if not args.no_batch:
+        batch = batch_benchmark(qxd, torch)
+        torch.cuda.empty_cache()
+    if not args.no_serve:
+        serve = serve_benchmark(qxd, torch)
+        torch.cuda.empty_cache()
 
     rec = _traffic_record(TRAFFIC_SOURCES)
     traffic = rec["bytes_per_launch"] if rec else None
@@ -1052,15 +1209,18 @@ def main():
                      "frac": gbs_rank / peak, "peak_source": peak_kind, "traffic": traffic,
                      "algorithmic_bytes": bps * V},
         "cpu_baseline": cpu,
+        "cpu_baseline_1core": cpu1,
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,
         "variants": variants,
         "solve": solve,
+        "batch": batch,
+        "serve": serve,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if args.no_solve:
+    if args.no_solve and args.no_batch and args.no_serve:
         lat.close()
     if ws > 1:
         dist.barrier()

@@ -256,13 +256,17 @@ int qxd_solve(qxd_lattice* lat, void* x, const void* b, const qxd_solver_params*
  * latency-bound paths where a cudaMalloc and the device synchronisation it
  * may imply are not acceptable, jobs that hold nearly all device memory).
  * The layout conversion goes through a fixed scratch array in the library's
- * device memory (2 x 12 MiB, reserved on every GPU that loads the library
- * until the process exits) instead of the scratch qxd_Dw allocates.
+ * device memory (2 x 12 MiB) instead of the scratch qxd_Dw allocates.
  * - flags: QXD_FP64 or QXD_FP32 only (device buffers, lexicographic layout).
  * - Lattices above 65536 simulated sites are rejected with QXD_ERR_ARG.
- * - The first call on a device looks up the scratch array's device address
- *   (cudaGetSymbolAddress) and keeps it; make that first call before any
- *   stream capture.
+ * - The first call on a device is its set-up: it looks up the scratch
+ *   array's device address (cudaGetSymbolAddress) and keeps it. Under CUDA's
+ *   lazy module loading (the default) that lookup is also what loads the
+ *   array onto the device, so the first call reserves the 24 MiB, and it
+ *   can fail with QXD_ERR_CUDA (out of memory) on a nearly full device.
+ *   Make the first call at set-up, while memory is available and before any
+ *   stream capture; the array then stays reserved until the process exits,
+ *   and later calls allocate nothing.
  * - Every call on a device shares the one scratch array, which keeps the
  *   last call's contents (each call overwrites all it reads): calls that
  *   overlap on the GPU (other streams, other threads) race and must be
@@ -294,10 +298,16 @@ int qxd_Dw_batch(int n, qxd_lattice* const* lats, void* const* out, const void* 
  * per vector operation for all active requests together; it then retires
  * finished requests and admits queued ones while the device memory of the
  * active requests stays within hbm_budget_bytes (a request larger than the
- * budget runs alone) and their number within max_active. A request's result
- * does not depend on the other requests in the batch (same kernels, grids
- * and reduction orders as alone). Work vectors come from the engine's
- * caching device allocator.
+ * budget runs alone) and their number within max_active. Each request is
+ * charged its largest footprint at admission: four FP64 fields, one FP32
+ * residual and params->nkv FP32 Krylov pairs, 24 V (4 * 8 + (1 + 2 nkv) * 4)
+ * bytes on a lattice of V sites. Work vectors come from the engine's caching
+ * device allocator, which keeps the bytes it holds (in use plus cached)
+ * within the budget by releasing cached blocks before it allocates more. A
+ * request whose work vectors cannot be allocated fails alone (its status is
+ * the error); the other requests go on. A request's result does not depend
+ * on the other requests in the batch (same kernels, grids and reduction
+ * orders as alone).
  * Buffers x and b (FP64, device; lexicographic unless params->flags has
  * QXD_LAYOUT_NATIVE) and the operator must stay valid until the request is
  * done (qxd_engine_poll). The paper solves one system at a time; this
@@ -505,6 +515,24 @@ size_t qxd_spinor_bytes(const qxd_lattice* lat, int prec);
 /* Lexicographic (device) -> native (device) and back, precision `prec`. */
 int qxd_spinor_pack(qxd_lattice* lat, void* native_out, const void* lex_in, int prec, void* stream);
 int qxd_spinor_unpack(qxd_lattice* lat, void* lex_out, const void* native_in, int prec, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Measurement aid: arithmetic throughput of the current GPU, the denominator
+ * of the rooflines of the kernels bound by FP64 or FP32 arithmetic (the FP64
+ * operator, the multi-shift CG and the Wilson flow; the FP32 Schwarz block
+ * solves). The paper has no counterpart.
+ * *flop_per_s = the fused multiply-add rate (2 flops per FMA) of a kernel in
+ * which every thread runs 16 independent chains of `iters` FMAs, 8 blocks of
+ * 256 threads per SM; best of three timed launches (CUDA events) after one
+ * untimed launch, on `stream` (NULL: the default stream). Synchronises.
+ * kind: QXD_PROBE_FMA64 (FP64 fma), QXD_PROBE_FMA32 (FP32 fmaf),
+ * QXD_PROBE_FMA32X2 (paired FP32 FMA on float2, two per instruction).
+ * QXD_ERR_ARG for an unknown kind, iters < 1 or a NULL result.
+ * ------------------------------------------------------------------------- */
+#define QXD_PROBE_FMA64 0
+#define QXD_PROBE_FMA32 1
+#define QXD_PROBE_FMA32X2 2
+int qxd_fma_rate(int kind, int iters, double* flop_per_s, void* stream);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char* qxd_last_error(void);

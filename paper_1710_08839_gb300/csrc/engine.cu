@@ -31,10 +31,14 @@ using Clock = std::chrono::steady_clock;
 
 constexpr long long kBigSites = 1 << 20;  // lattices routed to the single-lattice kernels
 
-// caching device allocator: freed blocks go to per-size free lists
+// caching device allocator: freed blocks go to per-size free lists. The
+// device memory it holds (blocks in use plus cached ones) is kept within
+// cap: before a new cudaMalloc would take it above cap, cached blocks of
+// other sizes are released first, then any cached block.
 struct DevicePool {
     std::map<size_t, std::vector<void*>> free_;
     size_t in_use = 0, held = 0;
+    size_t cap = (size_t)-1;
     int alloc(size_t bytes, void** p) {
         auto it = free_.find(bytes);
         if (it != free_.end() && !it->second.empty()) {
@@ -43,6 +47,7 @@ struct DevicePool {
             in_use += bytes;
             return QXD_OK;
         }
+        if (held + bytes > cap) reclaim(bytes);
         cudaError_t e = cudaMalloc(p, bytes);
         if (e != cudaSuccess) {
             trim();
@@ -60,6 +65,19 @@ struct DevicePool {
         if (!p) return;
         free_[bytes].push_back(p);
         in_use -= bytes;
+    }
+    // release cached blocks until a new block of `bytes` fits under cap:
+    // blocks of other sizes first (a block of this size would have been reused)
+    void reclaim(size_t bytes) {
+        for (int pass = 0; pass < 2 && held + bytes > cap; ++pass)
+            for (auto& kv : free_) {
+                if (pass == 0 && kv.first == bytes) continue;
+                while (!kv.second.empty() && held + bytes > cap) {
+                    cudaFree(kv.second.back());
+                    kv.second.pop_back();
+                    held -= kv.first;
+                }
+            }
     }
     void trim() {
         for (auto& kv : free_)
@@ -95,14 +113,15 @@ struct Job {
     cd c[BLAS_KMAX], a[BLAS_KMAX];
     qxd_solve_info info{};
     Clock::time_point t0;
+    size_t charge = 0;  // job_bytes charged against the budget while admitted
 };
 
-// device bytes a request is expected to hold: four FP64 fields, the FP32
-// residual and up to 6 Krylov pairs (allocated on demand)
+// device bytes a request holds at most: four FP64 fields, the FP32 residual
+// and nkv Krylov pairs (allocated on demand, but charged at admission so that
+// the active requests stay within the budget whatever their Krylov depth)
 size_t job_bytes(const qxd_lattice* op, int nkv) {
     const size_t V = (size_t)op->g.V;
-    const size_t pairs = nkv < 6 ? (size_t)nkv : 6;
-    return V * 24 * sizeof(double) * 4 + V * 24 * sizeof(float) * (1 + 2 * pairs);
+    return V * 24 * sizeof(double) * 4 + V * 24 * sizeof(float) * (1 + 2 * (size_t)nkv);
 }
 
 }  // namespace
@@ -122,6 +141,7 @@ struct Engine {
     SapGraphCache sap_graphs;  // graphs of the batched SAP launch sets
     SapWork sap_single;  // geometry of the single-lattice Schwarz path
     long long steps = 0;
+    size_t charged = 0;  // sum of the charges of the admitted requests
 
     ~Engine() {
         sap_graphs.release();
@@ -131,6 +151,8 @@ struct Engine {
     }
 
     void free_job(Job* j) {
+        charged -= j->charge;
+        j->charge = 0;
         pool.release(j->b64, j->f64_bytes);
         pool.release(j->x64, j->f64_bytes);
         pool.release(j->r64, j->f64_bytes);
@@ -183,8 +205,11 @@ struct Engine {
         std::vector<Job*> fresh;
         while (!pending.empty() && (int)active.size() + (int)fresh.size() < max_active) {
             Job* j = pending.front();
-            if (pool.in_use + job_bytes(j->op, j->P.nkv) > budget && !(active.empty() && fresh.empty())) break;
+            const size_t need = job_bytes(j->op, j->P.nkv);
+            if (charged + need > budget && !(active.empty() && fresh.empty())) break;
             pending.pop_front();
+            j->charge = need;
+            charged += need;
             int rc = alloc_job(j);
             if (rc) {
                 free_job(j);
@@ -239,9 +264,9 @@ struct Engine {
     static bool big(const Job* j) { return (long long)j->op->g.V >= kBigSites; }
 
     int step(int* ndone) {
-        int rc;
+        int rc, failed = 0;
         if ((rc = admit())) return rc;
-        const int n = (int)active.size();
+        int n = (int)active.size();
         if (n == 0) return QXD_OK;
         ++steps;
         if ((rc = red.ensure(n))) return rc;
@@ -261,12 +286,30 @@ struct Engine {
                 }
             if ((rc = blas_batch(red, B_D2F_NATIVE, m, 0, st))) return rc;
         }
-        // Krylov pair k of every job (allocated on first use)
-        for (Job* j : active)
-            if (!j->phi[j->k]) {
-                if ((rc = pool.alloc(j->f32_bytes, &j->phi[j->k])) || (rc = pool.alloc(j->f32_bytes, &j->chi[j->k])))
-                    return rc;
+        // Krylov pair k of every job (allocated on first use). A job whose
+        // pair cannot be allocated fails alone; the others go on.
+        {
+            std::vector<Job*> ok;
+            for (Job* j : active) {
+                if (!j->phi[j->k]) {
+                    int e = pool.alloc(j->f32_bytes, &j->phi[j->k]);
+                    if (!e) e = pool.alloc(j->f32_bytes, &j->chi[j->k]);
+                    if (e) {
+                        free_job(j);
+                        finish(j, e);
+                        continue;
+                    }
+                }
+                ok.push_back(j);
             }
+            if (ok.size() != active.size()) {
+                failed = (int)(active.size() - ok.size());
+                if (ndone) *ndone = failed;
+                active.swap(ok);
+                n = (int)active.size();
+                if (n == 0) return QXD_OK;
+            }
+        }
         // phi_k = P(rin)
         std::vector<SapJob> sj;
         for (Job* j : active) {
@@ -414,7 +457,8 @@ struct Engine {
                            !std::isfinite(j->rin_n);
             if (j->cycle_end) ending.push_back(j);
         }
-        if (!ending.empty() && (rc = end_cycles(ending))) return rc;
+        // a failure there still leaves every ending job finished or restarting
+        rc = ending.empty() ? QXD_OK : end_cycles(ending);
         // retire
         std::vector<Job*> still;
         int done = 0;
@@ -422,8 +466,8 @@ struct Engine {
             if (j->state == JOB_DONE) ++done;
             else still.push_back(j);
         active.swap(still);
-        if (ndone) *ndone = done;
-        return QXD_OK;
+        if (ndone) *ndone = done + failed;
+        return rc;
     }
 
     // x += sum beta phi, r = b - D x (FP64) for the jobs whose cycle ended
@@ -442,6 +486,23 @@ struct Engine {
             upd.push_back(j);
         }
         if (upd.empty()) return QXD_OK;
+        rc = update_cycles(upd);
+        if (rc) {
+            // no job may stay active with a finished cycle (k could be nkv):
+            // the jobs the update did not finish or restart fail with rc
+            for (Job* j : upd)
+                if (j->state != JOB_DONE && !j->restart) {
+                    free_job(j);
+                    finish(j, rc);
+                }
+        }
+        return rc;
+    }
+
+    // the FP64 update of end_cycles; every job of upd is processed by the
+    // final loop even when one completion fails (the first error is returned)
+    int update_cycles(std::vector<Job*>& upd) {
+        int rc;
         if ((rc = red.ensure((int)upd.size()))) return rc;
         for (size_t i = 0; i < upd.size(); ++i) {
             Job* j = upd[i];
@@ -483,6 +544,7 @@ struct Engine {
             b.out = j->r64;
         }
         if ((rc = blas_batch(red, B_SUB_NORM_F64, (int)upd.size(), 1, st))) return rc;
+        int first = QXD_OK;
         for (size_t i = 0; i < upd.size(); ++i) {
             Job* j = upd[i];
             j->rn = std::sqrt(red.h_res[i * 2 * BLAS_KMAX]);
@@ -493,14 +555,14 @@ struct Engine {
                 free_job(j);
                 finish(j, QXD_ERR_NUMERIC);
             } else if (j->rn <= j->target) {
-                if ((rc = complete(j, QXD_OK))) return rc;
+                if ((rc = complete(j, QXD_OK)) && !first) first = rc;
             } else if (j->info.iterations >= j->P.max_iter) {
-                if ((rc = complete(j, QXD_ERR_NOT_CONVERGED))) return rc;
+                if ((rc = complete(j, QXD_ERR_NOT_CONVERGED)) && !first) first = rc;
             } else {
                 j->restart = true;
             }
         }
-        return QXD_OK;
+        return first;
     }
 };
 
@@ -518,6 +580,7 @@ int qxd_engine_create(qxd_engine** out, size_t hbm_budget_bytes, int max_active,
     if (!e) return fail(QXD_ERR_OOM, "qxd_engine_create: host allocation failed");
     e->st = (cudaStream_t)stream;
     e->budget = hbm_budget_bytes;
+    e->pool.cap = hbm_budget_bytes;
     e->max_active = max_active;
     *out = e;
     return QXD_OK;

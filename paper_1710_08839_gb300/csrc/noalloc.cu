@@ -9,8 +9,13 @@
 // in advance, serving paths that cannot take the latency of a cudaMalloc
 // (which may synchronise the device), and jobs that already hold nearly all
 // device memory. For them this entry point keeps the two scratch fields in a
-// fixed array in the library's own device memory, reserved on every GPU when
-// the library is loaded, so a call allocates nothing.
+// fixed array in the library's own device memory, so a call allocates
+// nothing. The array belongs to this file's module, which holds no kernels:
+// with CUDA's lazy module loading (the default) the module, and so the
+// array, is loaded on a device by the first call there (its
+// cudaGetSymbolAddress), and it stays reserved until the process exits.
+// That first call is the set-up step: make it while memory is available and
+// before any stream capture; later calls only launch kernels.
 #include <mutex>
 
 #include "qxd_internal.cuh"
@@ -25,7 +30,7 @@ constexpr size_t kNoAllocFieldBytes = (size_t)kNoAllocMaxSites * 24 * sizeof(dou
 }  // namespace
 
 // Scratch of qxd_Dw_noalloc: input field, then output field (2 x 12 MiB).
-// Shared by every call on a device; see the contract in include/qxd.h.
+// Shared by every call on a device (the contract is in include/qxd.h).
 static __device__ __align__(256) unsigned char qxd_noalloc_scratch[2 * kNoAllocFieldBytes];
 
 namespace qxd {

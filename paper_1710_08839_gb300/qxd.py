@@ -135,6 +135,7 @@ SIGNATURES = {
     "qxd_spinor_bytes": (ctypes.c_size_t, [_vp, _i]),
     "qxd_spinor_pack": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_spinor_unpack": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "qxd_fma_rate": (_i, [_i, _i, ctypes.POINTER(_d), _vp]),
     "qxd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -291,6 +292,18 @@ def qxd_Dw_batch(lats, outs, ins, prec, rhs_per_site=0, stream=0) -> int:
     n = len(lats)
     arr = lambda xs: (_vp * max(n, 1))(*xs)
     return check(_call("qxd_Dw_batch", n, arr(lats), arr(outs), arr(ins), prec, rhs_per_site, stream))
+
+
+QXD_PROBE_FMA64 = 0
+QXD_PROBE_FMA32 = 1
+QXD_PROBE_FMA32X2 = 2
+
+
+def fma_rate(kind: int, iters: int, stream=None) -> float:
+    """qxd_fma_rate: FMA throughput (flop/s, 2 per FMA) of the current GPU."""
+    out = _d()
+    check(lib().qxd_fma_rate(int(kind), int(iters), ctypes.byref(out), _stream_ptr(stream)))
+    return out.value
 
 
 def qxd_last_error() -> str:

@@ -26,7 +26,7 @@ import oracle as O
 from oracle import qxd_rhmc as R
 import pins as P
 
-MU_HAT = 1.0e-3   # reading of the regulator of Table 2 (the paper does not print it)
+MU_HAT = 1.0e-3   # twisted-mass regulator of the QCD runs (Sec. 3 states mu_hat = 0.001)
 SPECTRUM = (1.98e-3, 7.62)  # range of |gamma5 D_hat| of the QCD2 rational approximation (App. A)
 
 

@@ -61,48 +61,81 @@ def test_views_share_the_gauge_field():
     parent.close()
 
 
+# operators of the batched-D test: two lattice sizes, two quarks on each,
+# three Gaussian right-hand sides per operator
+BATCH_LATTICES = (dict(T=8, L1=4, L2=4, L3=4, qhat=2), dict(T=8, L1=8, L2=8, L3=8, qhat=-1, seed=3))
+BATCH_QUARKS = ((0.05, -1), (0.1, 2))
+
+
+@pytest.fixture(scope="module")
+def batch_refs():
+    """Sources and the oracle's D applied to them, once for all parametrisations."""
+    rng = np.random.default_rng(9)
+    out = []
+    for kw in BATCH_LATTICES:
+        c = Case(**kw)
+        lo = O.Lattice(c.T, c.L1, c.L2, c.L3, c.mask)
+        g = O.GaugeField.from_physical(lo, c.su3.numpy(), c.ang.numpy())
+        for m0, q in BATCH_QUARKS:
+            op = O.Dirac(lo, g, m0, 1.0, 1.0, q)
+            for r in range(3):
+                src = rng.normal(size=(c.V, 4, 3)) + 1j * rng.normal(size=(c.V, 4, 3))
+                out.append((kw, m0, q, src, op.apply(src)))
+    return out
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("nr", [0, 1, 2, 4, 8])
-def test_batched_dw_matches_single(prec, nr):
+def test_batched_dw_matches_oracle(prec, nr, batch_refs):
+    """qxd_Dw_batch over 12 right-hand sides of 4 operators on 2 lattice
+    sizes, rhs_per_site nr (0: autotuned), against the oracle's D per
+    operator (FP64 1e-13 relative max, FP32 1e-5 relative norm) and against
+    qxd_Dw on the same input."""
     from paper_1710_08839_gb300 import qxd
     p = qxd.QXD_FP64 if prec == "fp64" else qxd.QXD_FP32
     dt = torch.complex128 if prec == "fp64" else torch.complex64
-    small = Case(T=8, L1=4, L2=4, L3=4, qhat=2)
-    big = Case(T=8, L1=8, L2=8, L3=8, qhat=-1, seed=3)   # different size
-    lats, ops = [], []
-    for c in (small, big):
+    lats, views = {}, {}
+    for kw in BATCH_LATTICES:
+        c = Case(**kw)
         par = c.lattice()
-        lats.append(par)
-        for m0, q in ((0.05, -1), (0.1, 2)):
+        lats[id(kw)] = par
+        for m0, q in BATCH_QUARKS:
             v = par.view()
             v.set_params(m0, 1.0, 1.0, q)
             v.sw_build()
-            ops.append((c, v))
-    rng = np.random.default_rng(9)
-    handles, ins, outs, refs = [], [], [], []
-    for c, v in ops:
-        for r in range(3):
-            src = torch.from_numpy(rng.normal(size=(c.V, 4, 3)) + 1j * rng.normal(size=(c.V, 4, 3))).to(dt).cuda()
-            xn = native(v, src, p)
-            yn = torch.empty_like(xn)
-            y = torch.empty_like(src)
-            v.Dw(y, src)
-            handles.append(v.handle)
-            ins.append(xn)
-            outs.append(yn)
-            refs.append((v, y))
+            views[(id(kw), m0, q)] = v
+    handles, ins, outs, checks = [], [], [], []
+    for kw, m0, q, src, ref in batch_refs:
+        v = views[(id(kw), m0, q)]
+        x = torch.from_numpy(src).to(dt).cuda()
+        xn = native(v, x, p)
+        yn = torch.empty_like(xn)
+        y = torch.empty_like(x)
+        v.Dw(y, x)
+        handles.append(v.handle)
+        ins.append(xn)
+        outs.append(yn)
+        checks.append((v, y, ref))
     qxd.qxd_Dw_batch(handles, [o.data_ptr() for o in outs], [i.data_ptr() for i in ins], p, nr,
                      torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
-    for (v, y), yn in zip(refs, outs):
+    for (v, y, ref), yn in zip(checks, outs):
         got = torch.empty_like(y)
         v.unpack(got, yn, p)
         a, b = got.cpu().numpy().astype(np.complex128), y.cpu().numpy().astype(np.complex128)
-        assert (rel_max(a, b) < 1e-13) if prec == "fp64" else (rel_norm(a, b) < 1e-6)
-    for _, v in ops:
+        if prec == "fp64":
+            assert rel_max(a, ref) < 1e-13
+            assert rel_max(a, b) < 1e-13
+        else:
+            assert rel_norm(a, ref) < 1e-5
+            assert rel_norm(a, b) < 1e-6
+    for v in views.values():
         v.close()
-    for l in lats:
+    for l in lats.values():
         l.close()
+
+
+ENGINE_QUARKS = ((0.05, -1), (0.1, 2))
 
 
 def _engine_setup():
@@ -113,13 +146,35 @@ def _engine_setup():
     reqs = []
     rng = np.random.default_rng(13)
     for c, par in ((a, pa), (b, pb)):
-        for m0, q in ((0.05, -1), (0.1, 2)):
+        for m0, q in ENGINE_QUARKS:
             v = par.view()
             v.set_params(m0, 1.0, 1.0, q)
             v.sw_build()
             bsrc = torch.from_numpy(rng.normal(size=(c.V, 4, 3)) + 1j * rng.normal(size=(c.V, 4, 3))).cuda()
-            reqs.append((c, v, bsrc))
+            reqs.append((c, v, bsrc, m0, q))
     return (pa, pb), reqs
+
+
+def _oracle_relres(c, m0, q, x, b):
+    """||b - D x|| / ||b|| with the oracle's D of request (c, m0, q)."""
+    lo = O.Lattice(c.T, c.L1, c.L2, c.L3, c.mask)
+    op = O.Dirac(lo, O.GaugeField.from_physical(lo, c.su3.numpy(), c.ang.numpy()), m0, 1.0, 1.0, q)
+    bb = b.cpu().numpy()
+    return float(np.linalg.norm(bb - op.apply(x.cpu().numpy())) / np.linalg.norm(bb))
+
+
+def _alone(v, b, **kw):
+    """The request solved alone, in a fresh engine."""
+    from paper_1710_08839_gb300 import qxd
+    e1 = qxd.Engine(hbm_budget_bytes=64 << 30, max_active=16)
+    x1 = torch.zeros_like(b)
+    rid = e1.submit(v, x1, b, tol=1e-10, **kw)
+    e1.run()
+    done, info = e1.poll(rid)
+    assert done and info["status"] == qxd.QXD_OK, info
+    e1.close()
+    torch.cuda.synchronize()
+    return x1
 
 
 def test_engine_results_same_alone_and_in_mix():
@@ -127,39 +182,99 @@ def test_engine_results_same_alone_and_in_mix():
     parents, reqs = _engine_setup()
     # all requests together
     eng = qxd.Engine(hbm_budget_bytes=64 << 30, max_active=16)
-    xs_mix = [torch.zeros_like(b) for _, _, b in reqs]
-    ids = [eng.submit(v, x, b, tol=1e-10) for (_, v, b), x in zip(reqs, xs_mix)]
+    xs_mix = [torch.zeros_like(b) for _, _, b, _, _ in reqs]
+    ids = [eng.submit(v, x, b, tol=1e-10) for (_, v, b, _, _), x in zip(reqs, xs_mix)]
     eng.run()
-    infos = []
     for rid in ids:
         done, info = eng.poll(rid)
         assert done and info["status"] == qxd.QXD_OK, info
         assert info["true_relres"] <= 1e-10
-        infos.append(info)
     # the batched SAP launch set is captured once per job mix and replayed
     gs = eng.graph_stats()
     assert gs["captures"] >= 1 and gs["replays"] >= 1, gs
     assert gs["captures"] + gs["replays"] <= eng.stats()["steps"], gs
     eng.close()
-    # each alone, in a fresh engine
-    for (c, v, b), xm in zip(reqs, xs_mix):
-        e1 = qxd.Engine(hbm_budget_bytes=64 << 30, max_active=16)
-        x1 = torch.zeros_like(b)
-        rid = e1.submit(v, x1, b, tol=1e-10)
-        e1.run()
-        assert e1.poll(rid)[0]
-        e1.close()
-        torch.cuda.synchronize()
-        assert torch.equal(x1, xm)
-    # the true residual with the oracle's D on the smaller lattice
-    c, v, b = reqs[0]
-    op = O.Dirac(O.Lattice(c.T, c.L1, c.L2, c.L3, c.mask),
-                 O.GaugeField.from_physical(O.Lattice(c.T, c.L1, c.L2, c.L3, c.mask), c.su3.numpy(), c.ang.numpy()),
-                 0.05, 1.0, 1.0, -1)
-    bb = b.cpu().numpy()
-    r = bb - op.apply(xs_mix[0].cpu().numpy())
-    assert np.linalg.norm(r) / np.linalg.norm(bb) < 2e-10
-    for _, v, _ in reqs:
+    for (c, v, b, m0, q), xm in zip(reqs, xs_mix):
+        # each alone, in a fresh engine: bit-identical
+        assert torch.equal(_alone(v, b), xm)
+        # every request's true residual with the oracle's D
+        assert _oracle_relres(c, m0, q, xm, b) < 2e-10
+    for _, v, _, _, _ in reqs:
+        v.close()
+    for p in parents:
+        p.close()
+
+
+def test_engine_staggered_arrivals():
+    """Continuous batching: two requests start, the engine steps, two more
+    arrive while the first two are on the GPU and join the running batch.
+    Every result equals the same request solved alone, bit for bit, and
+    passes the oracle's D."""
+    from paper_1710_08839_gb300 import qxd
+    parents, reqs = _engine_setup()
+    eng = qxd.Engine(hbm_budget_bytes=64 << 30, max_active=16)
+    xs = [torch.zeros_like(b) for _, _, b, _, _ in reqs]
+    first, later = (0, 2), (1, 3)     # one request of each lattice in each wave
+    ids = {}
+    for i in first:
+        _, v, b, _, _ = reqs[i]
+        ids[i] = eng.submit(v, xs[i], b, tol=1e-10)
+    for _ in range(2):
+        active, pending, done = eng.step()
+        assert active == 2 and pending == 0 and done == 0
+    for i in first:
+        assert not eng.poll(ids[i])[0]
+    for i in later:
+        _, v, b, _, _ = reqs[i]
+        ids[i] = eng.submit(v, xs[i], b, tol=1e-10)
+    active, pending, done = eng.step()
+    assert active + done == 4 and pending == 0     # admitted beside the running two
+    eng.run()
+    for i in range(4):
+        done, info = eng.poll(ids[i])
+        assert done and info["status"] == qxd.QXD_OK, info
+    eng.close()
+    for (c, v, b, m0, q), x in zip(reqs, xs):
+        assert torch.equal(_alone(v, b), x)
+        assert _oracle_relres(c, m0, q, x, b) < 2e-10
+    for _, v, _, _, _ in reqs:
+        v.close()
+    for p in parents:
+        p.close()
+
+
+def test_engine_budget_holds_with_full_krylov_depth():
+    """Requests with nkv = 16 under a budget of 2.5 of the larger requests:
+    the engine charges each its full Krylov depth, so the four requests (two
+    of 8192 sites, two of 16384) are never all active at once, and the bytes
+    in use and held by its allocator never exceed the budget."""
+    from paper_1710_08839_gb300 import qxd
+    parents, reqs = _engine_setup()
+    V = max(c.V for c, _, _, _, _ in reqs)
+    per_req = 24 * V * (4 * 8 + (1 + 2 * 16) * 4)
+    budget = int(2.5 * per_req)
+    eng = qxd.Engine(hbm_budget_bytes=budget, max_active=16)
+    xs = [torch.zeros_like(b) for _, _, b, _, _ in reqs]
+    # a loose inner tolerance and no SAP: many Krylov steps per cycle
+    ids = [eng.submit(v, x, b, tol=1e-10, nkv=16, precond=qxd.QXD_PRECOND_NONE, delta=0.0, max_iter=4000)
+           for (_, v, b, _, _), x in zip(reqs, xs)]
+    max_active = 0
+    while True:
+        a, p, d = eng.step()
+        st = eng.stats()
+        assert st["bytes_in_use"] <= budget and st["bytes_held"] <= budget, st
+        max_active = max(max_active, a)
+        if a == 0 and p == 0:
+            break
+    charge = {c.V: 24 * c.V * (4 * 8 + (1 + 2 * 16) * 4) for c, _, _, _, _ in reqs}
+    assert sum(charge[c.V] for c, _, _, _, _ in reqs) > budget     # not all four fit
+    assert 2 <= max_active < 4
+    for rid in ids:
+        done, info = eng.poll(rid)
+        assert done and info["status"] == qxd.QXD_OK, info
+        assert info["iterations"] > 16      # the Krylov space was filled at least once
+    eng.close()
+    for _, v, _, _, _ in reqs:
         v.close()
     for p in parents:
         p.close()
@@ -168,11 +283,11 @@ def test_engine_results_same_alone_and_in_mix():
 def test_engine_admission_by_budget_and_agreement_with_solve():
     from paper_1710_08839_gb300 import qxd
     parents, reqs = _engine_setup()
-    c, v, b = reqs[0]
+    c, v, b, _, _ = reqs[0]
     # budget below one request: requests run one at a time, all complete
     eng = qxd.Engine(hbm_budget_bytes=1 << 20, max_active=16)
-    xs = [torch.zeros_like(bb) for _, _, bb in reqs]
-    ids = [eng.submit(vv, x, bb, tol=1e-10) for (_, vv, bb), x in zip(reqs, xs)]
+    xs = [torch.zeros_like(bb) for _, _, bb, _, _ in reqs]
+    ids = [eng.submit(vv, x, bb, tol=1e-10) for (_, vv, bb, _, _), x in zip(reqs, xs)]
     max_active = 0
     while True:
         a, p, d = eng.step()
@@ -191,7 +306,7 @@ def test_engine_admission_by_budget_and_agreement_with_solve():
     rc, info = v.solve(x2, b, tol=1e-10, precond=qxd.QXD_PRECOND_SAP, inner_prec=qxd.QXD_FP32)
     assert rc == qxd.QXD_OK
     assert float((x2 - xs[0]).norm() / x2.norm()) < 1e-8
-    for _, vv, _ in reqs:
+    for _, vv, _, _, _ in reqs:
         vv.close()
     for p in parents:
         p.close()

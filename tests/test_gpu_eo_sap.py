@@ -65,16 +65,20 @@ def test_even_odd_operators(name, prec):
 SAP_CASES = {
     # smallest C* lattice the 4^4 block colouring admits: 8 x 16 x 8 x 8
     "cstar_8x16x8x8_q2": dict(T=8, L1=8, L2=8, L3=8, qhat=2, m0=0.3),
+    # qhat = 0: the kernels' template without the U(1) phases
+    "cstar_8x16x8x8_q0": dict(T=8, L1=8, L2=8, L3=8, qhat=0, m0=0.1),
     "periodic_8x8x8x8_q-1": dict(T=8, L1=8, L2=8, L3=8, mask=0, qhat=-1, m0=0.1),
 }
 
 
+@pytest.mark.parametrize("ncy,nmr", [(2, 3), (5, 5)])
 @pytest.mark.parametrize("name", list(SAP_CASES))
-def test_sap_matches_oracle(name):
-    from paper_1710_08839_gb300 import qxd
+def test_sap_matches_oracle(name, ncy, nmr):
+    """qxd_sap against the oracle's Schwarz method, FP64 to 1e-12 relative
+    max and FP32 to 1e-5 relative norm; (5, 5) is the solver workload's
+    setting (5 cycles, 5 minimal-residual steps)."""
     c = Case(**SAP_CASES[name])
     op = c.oracle()
-    ncy, nmr = 2, 3
     ref = O.sap(op, c.psi.numpy(), ncy, nmr)
     lat = c.lattice()
     for dt, tol in ((torch.complex128, 1e-12), (torch.complex64, 1e-5)):

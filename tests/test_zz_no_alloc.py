@@ -1,7 +1,9 @@
 """qxd_Dw_noalloc: D without device allocation, for callers that cannot let a
-library allocate during a call. It is checked against qxd_Dw (the entry point
-that allocates its conversion scratch) on two calls in a row, and its size
-limit is checked. Collected last on purpose."""
+library allocate during a call (their own memory pools, nearly full
+devices, paths that cannot wait for a cudaMalloc). Two calls in a row are
+checked to leave the device's free memory unchanged and against qxd_Dw (the
+entry point that allocates its conversion scratch); the size limit is
+checked too. Collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -31,19 +33,31 @@ def _noalloc(lat, out, inp, prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_noalloc_matches_Dw_on_two_calls(prec):
+    """On a fresh lattice: one set-up call, then two calls in a row that must
+    leave the device's free memory unchanged (nothing allocated, not even the
+    conversion scratch qxd_Dw would create), then both results against
+    qxd_Dw."""
     from paper_1710_08839_gb300 import qxd
     p = qxd.QXD_FP64 if prec == "fp64" else qxd.QXD_FP32
     dt = torch.complex128 if prec == "fp64" else torch.complex64
     c = Case(T=8, L1=4, L2=4, L3=4, eps=0.4, sigma=0.5, m0=0.2, qhat=-1)
     lat = c.lattice()
     rng = np.random.default_rng(17)
-    for call in range(2):
-        src = c.psi.numpy() if call == 0 else rng.normal(size=(c.V, 4, 3)) + 1j * rng.normal(size=(c.V, 4, 3))
-        x = torch.from_numpy(np.ascontiguousarray(src)).to(dt).cuda()
+    srcs = [c.psi.numpy(), rng.normal(size=(c.V, 4, 3)) + 1j * rng.normal(size=(c.V, 4, 3))]
+    xs = [torch.from_numpy(np.ascontiguousarray(s)).to(dt).cuda() for s in srcs]
+    ys = [torch.full_like(x, float("nan")) for x in xs]
+    # set-up call: the first call on a device loads the scratch array
+    warm = torch.empty_like(xs[0])
+    assert _noalloc(lat, warm, xs[0], p) == qxd.QXD_OK, qxd.qxd_last_error()
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    for x, y in zip(xs, ys):
+        assert _noalloc(lat, y, x, p) == qxd.QXD_OK, qxd.qxd_last_error()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before
+    for x, y in zip(xs, ys):
         ref = torch.empty_like(x)
         lat.Dw(ref, x)
-        y = torch.full_like(x, float("nan"))
-        assert _noalloc(lat, y, x, p) == qxd.QXD_OK, qxd.qxd_last_error()
         torch.cuda.synchronize()
         a, b = y.cpu().numpy().astype(np.complex128), ref.cpu().numpy().astype(np.complex128)
         assert np.isfinite(a).all()
