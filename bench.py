@@ -207,7 +207,7 @@ def write_traffic_record(csv_path):
            "algorithmic_bytes_per_launch": BYTES_PER_SITE_FP32[True] * V,
            "duration_ns_under_ncu": statistics.mean(v["gpu__time_duration.sum"] for v in per.values()),
            "command": "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
-                      "--clock-control none -k regex:k_dirac -s 3 -c 5 --csv --log-file dirac_full_dram.csv "
+                      "--clock-control none -k regex:k_dirac -s 52 -c 5 --csv --log-file dirac_full_dram.csv "
                       "python bench.py --steps 20 --warmup 3 --no-cpu-baseline --no-solve --no-variants --no-e2e",
            "source_sha256": h.hexdigest(),
            "note": "full benchmark size, 1-pass metrics; stale once the kernel sources change"}
@@ -800,6 +800,52 @@ def alu_benchmark(qxd, torch):
     return out
 
 
+def oracle_benchmark(qxd, torch):
+    """The FP64 oracle on this machine's host cores: the small workload's
+    plain GCR solve to 1e-12 (one core), and the oracle's D at sampled sites
+    of the throughput and solver workloads on one core and on all cores, from
+    which the time of one FP64 D application and of a plain FP64 GCR solve of
+    the solver workload are estimated (the oracle cannot finish that solve in
+    a bench run)."""
+    import numpy as np
+
+    import oracle as O
+    import synth
+    out = {}
+    # small workload: doubled 8x8x4x4 (L=4, T=8), q=-1, m0=0.2, eps 0.4, sigma 0.5
+    T, L = 8, 4
+    lat = O.Lattice(T, L, L, L, 0b1110)
+    su3 = synth.su3_field(T, L, L, L, 0.4, synth.SEED_GAUGE).numpy()
+    ang = synth.u1_field(T, L, L, L, 0.5, synth.SEED_GAUGE + 500).numpy()
+    b = synth.spinor_field(T, 2 * L, L, L, synth.SEED_SOURCE).reshape(-1, 4, 3).numpy()
+    op = O.Dirac(lat, O.GaugeField.from_physical(lat, su3, ang), 0.2, 1.0, 1.0, -1)
+    op.apply(b)  # clover matrices of the small lattice built once
+    t0 = time.perf_counter()
+    _, it, res = O.gcr(op.apply, b, tol=1e-12)
+    out["small_gcr_1e-12"] = {"seconds": time.perf_counter() - t0, "iterations": it, "relres": res, "cores": 1,
+                              "workload": "doubled 8x8x4x4 C* lattice (L=4, T=8), qhat=-1, m0=0.2, nkv 16"}
+    for name, w in (("throughput", WORKLOAD), ("solver", dict(WORKLOADS["solve"], m0=0.05, qhat=-1))):
+        su3, ang, psi, V = make_inputs("cuda", w)
+        su3h, angh, psih = su3.cpu().numpy(), ang.cpu().numpy(), psi.numpy()
+        del su3, ang
+        r1, n1, t1 = oracle_sample_rate(su3h, angh, psih, V, w, target_s=8.0)
+        ra, na, ta, cores = oracle_sample_rate_all_cores(su3h, angh, psih, V, w, target_s=10.0)
+        row = {"sites": V, "one_core_sites_per_s": r1, "all_cores_sites_per_s": ra, "cores": cores,
+               "one_core_apply_s": V / r1, "all_cores_apply_s": V / ra,
+               "fp64_GB_per_s_one_core": r1 * BYTES_PER_SITE_FP64[True] / 1e9,
+               "fp64_GB_per_s_all_cores": ra * BYTES_PER_SITE_FP64[True] / 1e9}
+        if name == "solver":
+            # the plain FP64 GCR (nkv 16) of the GPU needs 119 steps and 8 restarts
+            # at this point (m0 = 0.05, qhat = -1): one D per step and per restart
+            applies = 119 + 8
+            row["plain_gcr_1e-10_estimate_s_all_cores"] = applies * V / ra
+            row["estimate_note"] = (f"{applies} applications of D (the GPU's plain FP64 GCR to 1e-10 at "
+                                    "m0=0.05, qhat=-1: 119 steps, 8 restarts) x the all-cores time of one")
+        out[name] = row
+        del su3h, angh, psih
+    return out
+
+
 def sap_benchmark(qxd, torch, steps, w):
     """Time one FP32 SAP application (ncy 5, nmr 5) on the lattice of workload w."""
     su3, ang, psi, V = make_inputs("cuda", w)
@@ -1021,12 +1067,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
     ap.add_argument("--mode", default="dw",
-                    choices=["dw", "solve", "sap", "batch", "serve", "rational", "flow", "dfl", "alu"],
+                    choices=["dw", "solve", "sap", "batch", "serve", "rational", "flow", "dfl", "alu", "oracle"],
                     help="dw: the Dw throughput line (plus a solver summary unless --no-solve); "
                          "solve: solver comparison only; sap: time the SAP preconditioner only; "
                          "batch / serve: multi-RHS and serving workloads; rational: pseudofermion action; "
                          "flow: Wilson flow and gauge observables; dfl: deflated vs SAP solver; "
-                         "alu: FP64/FP32 FMA throughput (the ALU roofline denominators)")
+                         "alu: FP64/FP32 FMA throughput (the ALU roofline denominators); "
+                         "oracle: the FP64 oracle timed on the host cores")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the multi-RHS summary of the default line")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving summary of the default line")
@@ -1052,8 +1099,10 @@ def main():
     ge.build()
     from paper_1710_08839_gb300 import qxd
 
-    if args.mode in ("solve", "sap", "batch", "serve", "rational", "flow", "dfl", "alu"):
-        if args.mode == "alu":
+    if args.mode in ("solve", "sap", "batch", "serve", "rational", "flow", "dfl", "alu", "oracle"):
+        if args.mode == "oracle":
+            res = oracle_benchmark(qxd, torch)
+        elif args.mode == "alu":
             res = alu_benchmark(qxd, torch)
         elif args.mode == "dfl":
             res = dfl_benchmark(qxd, torch)
@@ -1118,6 +1167,7 @@ def main():
         # warm up for >= 1 s so the sampler is running when the timed region starts
         ms = time_applies(qxd.QXD_FP32, xn, yn, args.steps, args.warmup, min_warm_s=1.0)
     clocks = clk.summary(window["t0"], window["t1"])
+    shape = lat.dw_shape(qxd.QXD_FP32)  # chosen by the autotuner on the first application
     bps = BYTES_PER_SITE_FP32[True]
     gbs_rank = bps * V / (ms * 1e-3) / 1e9
     value = aggregate_value(bps * V / 1e9, ms * 1e-3, ws)
@@ -1214,6 +1264,7 @@ def main():
         "gpu_launches": args.steps,
         "clocks": clocks,
         "variants": variants,
+        "autotune": {"timed_shape": shape, "choices": [l for l in qxd.tune_report().splitlines() if l]},
         "solve": solve,
         "batch": batch,
         "serve": serve,

@@ -179,7 +179,10 @@ int qxd_eo_reconstruct(qxd_lattice* lat, void* x, const void* b, int flags, void
  * to the block (hops leaving the block dropped). Starts from out = 0.
  * flags: precision and layout as for qxd_Dw, device buffers only. The
  * lattice needs every extent a multiple of 8 and, with C* boundaries,
- * L1 a multiple of 4 with L_k/4 + L1/4 even (else QXD_ERR_ARG).
+ * L1 a multiple of 4 with L_k/4 + L1/4 even (else QXD_ERR_ARG). The first
+ * FP32 application on a lattice (here or inside qxd_solve) allocates an FP32
+ * residual field (96 bytes per site), kept with the lattice until
+ * qxd_lattice_destroy.
  */
 int qxd_sap(qxd_lattice* lat, void* out, const void* in, int ncy, int nmr, int flags, void* stream);
 
@@ -515,6 +518,37 @@ size_t qxd_spinor_bytes(const qxd_lattice* lat, int prec);
 /* Lexicographic (device) -> native (device) and back, precision `prec`. */
 int qxd_spinor_pack(qxd_lattice* lat, void* native_out, const void* lex_in, int prec, void* stream);
 int qxd_spinor_unpack(qxd_lattice* lat, void* lex_out, const void* native_in, int prec, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Launch-shape autotuning of D (qxd_Dw and every internal full-lattice D, as
+ * in the solvers). The paper has no counterpart. A shape is the hop order
+ * (software-pipelined: the loads of the next hop issued before the
+ * arithmetic of this one, 128 registers, FP32 only; or plain), the threads
+ * per block (64 or 128) and the sweep window (rows of x2 per chunk of the
+ * tiled site order, a divisor of L2). With the autotuner on (the default),
+ * the first D on a lattice shape (extents, C* mask, precision, qhat != 0)
+ * times every candidate shape on that call's input (three launches each,
+ * CUDA events, synchronising the stream once) and keeps the fastest for the
+ * shape, process-wide; with it off, the first call takes the default shape
+ * (pipelined in FP32, 128 threads, the largest window up to 64K sites). The
+ * output of every call comes from the chosen shape; all shapes compute the
+ * same per-site sums in the same order. A first call inside a stream
+ * capture must not tune: pin the shape (qxd_dw_set_shape) or make a first
+ * call before the capture.
+ * ------------------------------------------------------------------------- */
+/* enable = 0 or 1; returns the previous setting */
+int qxd_set_autotune(int enable);
+/* the shape chosen for lat's lattice shape and precision; ms = the time of
+ * one application when tuned (0 otherwise). QXD_ERR_STATE if none yet. Any
+ * output pointer may be NULL. */
+int qxd_dw_shape(const qxd_lattice* lat, int prec, int* pipelined, int* threads, int* rows, float* ms);
+/* pin a shape for lat's lattice shape and precision (QXD_ERR_ARG: pipelined
+ * not 0/1 or set with FP64, threads not 64/128, rows not dividing L2) */
+int qxd_dw_set_shape(const qxd_lattice* lat, int prec, int pipelined, int threads, int rows);
+/* every choice made so far (D shapes and the batched D's right-hand sides
+ * per site), one per line, as text in buf (truncated to len - 1 characters,
+ * NUL-terminated); *needed = the full length + 1. buf may be NULL. */
+int qxd_tune_report(char* buf, size_t len, size_t* needed);
 
 /* ---------------------------------------------------------------------------
  * Measurement aid: arithmetic throughput of the current GPU, the denominator

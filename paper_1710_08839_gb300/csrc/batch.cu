@@ -17,8 +17,11 @@
 #include <tuple>
 #include <vector>
 
+#include <cstdio>
+
 #include "batch.cuh"
 #include "dirac_common.cuh"
+#include "tune.cuh"
 
 namespace qxd {
 
@@ -217,6 +220,16 @@ int dw_batch(const std::vector<BatchItem>& items, int prec, int nr, cudaStream_t
         }
     }
     return prec == QXD_FP32 ? launch_batch<float>(items, nr, st) : launch_batch<double>(items, nr, st);
+}
+
+void dw_batch_report(std::string& out) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    char line[160];
+    for (const auto& kv : g_tuned) {
+        std::snprintf(line, sizeof line, "Dw_batch %s volume<=2^%d: rhs_per_site=%d (tuned)\n",
+                      kv.first.first == QXD_FP32 ? "fp32" : "fp64", kv.first.second, kv.second);
+        out += line;
+    }
 }
 
 int dw_batch_tuned_nr(int prec, int volume) {

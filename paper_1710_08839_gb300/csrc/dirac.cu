@@ -5,19 +5,50 @@
 // which is Eqs. (18)-(20) expanded (the diagonal 4 of Dw moved into M).
 // One thread per site; spin projection to half spinors before the colour
 // multiplication (the projectors commute with W). FP32: links as two rows
-// plus the U(1) angle; FP64: full links. Both parities in one sweep, in the
-// tiled order of sweep_coords so neighbour data is reused from L2.
+// plus the U(1) angle, hops software-pipelined (k_dirac32); FP64: full links.
+// Both parities in one sweep, in the tiled order of sweep_coords so
+// neighbour data is reused from L2.
 //
 // Chiral basis, psi = (psi0, psi1 | psi2, psi3):
 //   (1 -+ g0): h = (psi0 +- psi2, psi1 +- psi3),   lower = (+-h0, +-h1)
 //   (1 -+ g1): h = (psi0 +- i psi3, psi1 +- i psi2), lower = (-+i h1, -+i h0)
 //   (1 -+ g2): h = (psi0 +- psi3, psi1 -+ psi2),   lower = (-+h1, +-h0)
 //   (1 -+ g3): h = (psi0 +- i psi2, psi1 -+ i psi3), lower = (-+i h0, +-i h1)
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
 #include "dirac_common.cuh"
+#include "tune.cuh"
 
 namespace qxd {
 
 namespace {
+
+// FP32: the pipelined hop order of hops_pipelined (128 registers)
+template <bool QNZ>
+__global__ void __launch_bounds__(DW_THREADS, DW_PP_MIN_BLOCKS) k_dirac32(Geom g, Fields<float> f, float q) {
+    const int tau = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tau >= g.V) return;
+    int x0, x1, x2, x3;
+    sweep_coords(g, tau, x0, x1, x2, x3);
+    const int p = (x0 + x1 + x2 + x3) & 1;
+    const int s = native_index(g, lex_index(g, x0, x1, x2, x3), p);
+    int nb[8];
+    neighbours8(g, x0, x1, x2, x3, 1 - p, nb);
+    cplx<float> acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = mk(0.f, 0.f);
+    hops_pipelined<QNZ>(f, g.V, s, nb, q, acc);
+    cplx<float> v[12], w[12];
+    load_spinor(f.psi, g.V, s, v);
+    clover_mul<true>(f.C, g.V, s, v, w);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) w[i] = w[i] - 0.5f * acc[i];
+    store_spinor_cs(f.out, g.V, s, w);
+}
 
 template <typename R, bool QNZ>
 __global__ void __launch_bounds__(DW_THREADS, DwMinBlocks<R>::value) k_dirac(Geom g, Fields<R> f, R q) {
@@ -76,21 +107,102 @@ __global__ void k_unpack(Geom g, const typename Fields<R>::vec* __restrict__ nat
 
 }  // namespace
 
-int launch_dirac(qxd_lattice* lat, void* out, const void* in, int prec, cudaStream_t st) {
-    const Geom& g = lat->g;
-    const int blocks = (g.V + DW_THREADS - 1) / DW_THREADS;
+namespace {
+
+// D with launch shape sh (hop order, threads per block, sweep window)
+int launch_dirac_shape(qxd_lattice* lat, void* out, const void* in, int prec, const DwShape& sh, cudaStream_t st) {
+    Geom g = lat->g;
+    g.R = sh.rows;
+    const int blocks = (g.V + sh.threads - 1) / sh.threads;
     const bool qnz = lat->qhat != 0;
     if (prec == QXD_FP32) {
         Fields<float> f{(const float4*)in, (float4*)out, lat->U32, lat->A32, lat->C32};
-        if (qnz) k_dirac<float, true><<<blocks, DW_THREADS, 0, st>>>(g, f, (float)lat->qhat);
-        else k_dirac<float, false><<<blocks, DW_THREADS, 0, st>>>(g, f, 0.f);
+        if (sh.pipelined) {
+            if (qnz) k_dirac32<true><<<blocks, sh.threads, 0, st>>>(g, f, (float)lat->qhat);
+            else k_dirac32<false><<<blocks, sh.threads, 0, st>>>(g, f, 0.f);
+        } else {
+            if (qnz) k_dirac<float, true><<<blocks, sh.threads, 0, st>>>(g, f, (float)lat->qhat);
+            else k_dirac<float, false><<<blocks, sh.threads, 0, st>>>(g, f, 0.f);
+        }
     } else {
         Fields<double> f{(const double2*)in, (double2*)out, lat->U64, lat->Zq64, lat->C64};
-        if (qnz) k_dirac<double, true><<<blocks, DW_THREADS, 0, st>>>(g, f, (double)lat->qhat);
-        else k_dirac<double, false><<<blocks, DW_THREADS, 0, st>>>(g, f, 0.0);
+        if (qnz) k_dirac<double, true><<<blocks, sh.threads, 0, st>>>(g, f, (double)lat->qhat);
+        else k_dirac<double, false><<<blocks, sh.threads, 0, st>>>(g, f, 0.0);
     }
     QXD_LAUNCHED("k_dirac");
     return QXD_OK;
+}
+
+// candidate sweep windows: divisors R of N2 with a window of N1 R N3 sites
+// between 16K and 256K, the default (largest window <= 64K) and its nearest
+// neighbours among them
+std::vector<int> window_candidates(const Geom& g) {
+    std::vector<int> ok;
+    for (int R = 1; R <= g.N2; ++R) {
+        const long long w = (long long)g.N1 * R * g.N3;
+        if (g.N2 % R == 0 && w >= 16384 && w <= 262144) ok.push_back(R);
+    }
+    std::vector<int> out;
+    int at = -1;
+    for (int i = 0; i < (int)ok.size(); ++i)
+        if (ok[i] == g.R) at = i;
+    if (at < 0) return {g.R};
+    for (int i = std::max(0, at - 1); i <= std::min((int)ok.size() - 1, at + 1); ++i) out.push_back(ok[i]);
+    return out;
+}
+
+// time every candidate shape on this call's input (3 launches each after
+// one untimed launch) and return the fastest
+int tune_dirac(qxd_lattice* lat, void* out, const void* in, int prec, cudaStream_t st, DwShape* best) {
+    std::vector<DwShape> cand;
+    const std::vector<int> rows = window_candidates(lat->g);
+    for (int pl = (prec == QXD_FP32 ? 1 : 0); pl >= 0; --pl)
+        for (int th : {128, 64})
+            for (int R : rows) cand.push_back(DwShape{pl, th, R, 0.f});
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    QXD_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(QXD_ERR_CUDA, "autotune: cudaEventCreate");
+    }
+    int rc = QXD_OK;
+    best->ms = 0.f;
+    for (DwShape& c : cand) {
+        if ((rc = launch_dirac_shape(lat, out, in, prec, c, st))) break;
+        cudaEventRecord(e0, st);
+        for (int rep = 0; rep < 3 && !rc; ++rep) rc = launch_dirac_shape(lat, out, in, prec, c, st);
+        if (rc) break;
+        cudaEventRecord(e1, st);
+        const cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "autotune: cudaEventSynchronize");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        c.ms = ms / 3;
+        if (best->ms == 0.f || c.ms < best->ms) *best = c;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+}  // namespace
+
+int launch_dirac(qxd_lattice* lat, void* out, const void* in, int prec, cudaStream_t st) {
+    const DwKey key = dw_key(lat, prec);
+    DwShape sh;
+    if (!dw_shape_get(key, &sh)) {
+        if (autotune_enabled()) {
+            int rc = tune_dirac(lat, out, in, prec, st, &sh);
+            if (rc) return rc;
+        } else {
+            sh = dw_default_shape(lat, prec);
+        }
+        dw_shape_put(key, sh, autotune_enabled() ? "tuned" : "default");
+    }
+    return launch_dirac_shape(lat, out, in, prec, sh, st);
 }
 
 int launch_pack(qxd_lattice* lat, void* nat, const void* lex, int prec, cudaStream_t st) {

@@ -10,10 +10,12 @@ namespace qxd {
 
 constexpr int DW_THREADS = 128;
 
-// Register budget of the stencil kernels: FP32 at most 80 registers (6 blocks
-// of 128 threads per SM); the kernels are latency bound and more resident
-// warps keep more loads in flight. FP64 at most 128 (4 blocks). Blocks of
-// 128 threads measured faster than 256 or 64 at the same budget.
+// Register budget of the stencil kernels in the plain hop order: FP32 at most
+// 80 registers (6 blocks of 128 threads per SM); the kernels are latency bound
+// and more resident warps keep more loads in flight. FP64 at most 128 (4
+// blocks). Blocks of 128 threads measured faster than 256 or 64 at the same
+// budget. The pipelined FP32 hop order below (hops_pipelined) runs at 128
+// registers instead.
 template <typename R>
 struct DwMinBlocks {
     static constexpr int value = sizeof(R) == 4 ? 6 : 4;
@@ -290,5 +292,113 @@ __device__ __forceinline__ void dirac_dir(const Geom& g, const Fields<R>& f,
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 hopping term with software pipelining. The eight hops of a site are
+// taken in the order (mu, fwd), (mu, bwd), mu = 0..3; the loads of hop k + 1
+// (neighbour spinor, link, angle) are issued before the arithmetic of hop k,
+// so that every thread keeps one hop's loads in flight while it computes.
+// The stencil is bound by load latency: with 128 registers (4 blocks of 128
+// threads per SM) this moves more bytes than the plain order at 80 registers
+// and 6 blocks per SM.
+// ---------------------------------------------------------------------------
+constexpr int DW_PP_MIN_BLOCKS = 4;
+
+struct HopData {
+    float4 sp[6];  // neighbour spinor
+    float4 lk[3];  // rows 0, 1 of the link
+    float ang;     // U(1) angle of the link
+};
+
+// neighbour native indices: nb[2 mu] = x + mu, nb[2 mu + 1] = x - mu
+__device__ __forceinline__ void neighbours8(const Geom& g, int x0, int x1, int x2, int x3, int po, int nb[8]) {
+    nb[0] = native_index(g, neighbour_lex<0, +1>(g, x0, x1, x2, x3), po);
+    nb[1] = native_index(g, neighbour_lex<0, -1>(g, x0, x1, x2, x3), po);
+    nb[2] = native_index(g, neighbour_lex<1, +1>(g, x0, x1, x2, x3), po);
+    nb[3] = native_index(g, neighbour_lex<1, -1>(g, x0, x1, x2, x3), po);
+    nb[4] = native_index(g, neighbour_lex<2, +1>(g, x0, x1, x2, x3), po);
+    nb[5] = native_index(g, neighbour_lex<2, -1>(g, x0, x1, x2, x3), po);
+    nb[6] = native_index(g, neighbour_lex<3, +1>(g, x0, x1, x2, x3), po);
+    nb[7] = native_index(g, neighbour_lex<3, -1>(g, x0, x1, x2, x3), po);
+}
+
+// loads of hop k at site s (forward: link and angle of s; backward: of the
+// neighbour sn); a_own = the four angles of s
+__device__ __forceinline__ void hop_load(const Fields<float>& f, int V, int k, int s, int sn, const float4& a_own,
+                                         HopData& d) {
+    const int mu = k >> 1;
+    const bool fwd = (k & 1) == 0;
+    const int sl = fwd ? s : sn;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) d.sp[c] = f.psi[(size_t)c * V + sn];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) d.lk[j] = f.U[((size_t)mu * 3 + j) * V + sl];
+    if (fwd) d.ang = mu == 0 ? a_own.x : mu == 1 ? a_own.y : mu == 2 ? a_own.z : a_own.w;
+    else d.ang = reinterpret_cast<const float*>(f.A + sn)[mu];
+}
+
+// raw hop (without the factor -1/2) added to acc: (1 - DIR g_mu) W psi(x + DIR mu)
+// with W = U z^qhat forwards and its adjoint backwards
+template <bool QNZ, int MU, int DIR>
+__device__ __forceinline__ void hop_compute(const HopData& d, float q, cplx<float> acc[12]) {
+    cplx<float> v[12], h0[3], h1[3], g0[3], g1[3], u[3][3];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        v[2 * c] = mk(d.sp[c].x, d.sp[c].y);
+        v[2 * c + 1] = mk(d.sp[c].z, d.sp[c].w);
+    }
+    project<float, MU, DIR>(v, h0, h1);
+    u[0][0] = mk(d.lk[0].x, d.lk[0].y);
+    u[0][1] = mk(d.lk[0].z, d.lk[0].w);
+    u[0][2] = mk(d.lk[1].x, d.lk[1].y);
+    u[1][0] = mk(d.lk[1].z, d.lk[1].w);
+    u[1][1] = mk(d.lk[2].x, d.lk[2].y);
+    u[1][2] = mk(d.lk[2].z, d.lk[2].w);
+    u[2][0] = conj(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
+    u[2][1] = conj(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
+    u[2][2] = conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
+    if (DIR > 0) {
+        su3_mul(u, h0, g0);
+        su3_mul(u, h1, g1);
+    } else {
+        su3_dag_mul(u, h0, g0);
+        su3_dag_mul(u, h1, g1);
+    }
+    if (QNZ) {
+        // exp(i qhat A), argument reduced to [-pi, pi] as in link_phase
+        float t = q * d.ang;
+        const float kk = rintf(t * 0.15915494309189535f);
+        t = fmaf(-kk, 6.2831853071795865f, t);
+        float sn, cs;
+        __sincosf(t, &sn, &cs);
+        const cplx<float> ph = mk(cs, DIR > 0 ? sn : -sn);
+        times3(ph, g0);
+        times3(ph, g1);
+    }
+    accumulate<float, MU, DIR>(acc, g0, g1);
+}
+
+// acc += raw sum of the eight hops at site s with neighbours nb
+template <bool QNZ>
+__device__ __forceinline__ void hops_pipelined(const Fields<float>& f, int V, int s, const int nb[8], float q,
+                                               cplx<float> acc[12]) {
+    const float4 a_own = QNZ ? f.A[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+    HopData d[2];
+    hop_load(f, V, 0, s, nb[0], a_own, d[0]);
+    hop_load(f, V, 1, s, nb[1], a_own, d[1]);
+    hop_compute<QNZ, 0, +1>(d[0], q, acc);
+    hop_load(f, V, 2, s, nb[2], a_own, d[0]);
+    hop_compute<QNZ, 0, -1>(d[1], q, acc);
+    hop_load(f, V, 3, s, nb[3], a_own, d[1]);
+    hop_compute<QNZ, 1, +1>(d[0], q, acc);
+    hop_load(f, V, 4, s, nb[4], a_own, d[0]);
+    hop_compute<QNZ, 1, -1>(d[1], q, acc);
+    hop_load(f, V, 5, s, nb[5], a_own, d[1]);
+    hop_compute<QNZ, 2, +1>(d[0], q, acc);
+    hop_load(f, V, 6, s, nb[6], a_own, d[0]);
+    hop_compute<QNZ, 2, -1>(d[1], q, acc);
+    hop_load(f, V, 7, s, nb[7], a_own, d[1]);
+    hop_compute<QNZ, 3, +1>(d[0], q, acc);
+    hop_compute<QNZ, 3, -1>(d[1], q, acc);
+}
 
 }  // namespace qxd

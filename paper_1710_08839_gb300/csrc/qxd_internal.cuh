@@ -250,6 +250,7 @@ struct qxd_lattice {
     void* scratch_in = nullptr;   // native spinor FP64-sized
     void* scratch_out = nullptr;  // native spinor FP64-sized
     void* scratch_lex = nullptr;  // lexicographic FP64 spinor
+    float4* sap_r = nullptr;      // FP32 residual of the Schwarz method (first FP32 SAP application)
 
     qxd::SolverWork* solver = nullptr;  // Krylov work vectors (first solve)
     qxd::MscgWork* mscg = nullptr;      // multi-shift CG work vectors (first use)

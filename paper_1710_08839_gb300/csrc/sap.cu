@@ -12,11 +12,15 @@
 //         even-odd form D_hat_B = M_ee - H_eo M_oo^-1 H_oe of the block
 //   psi_B += delta
 // Starting from psi = 0, ncy cycles give psi = SAP(eta).
-// FP32 (k_sap_split, k_sap_block_batch): two threads per site pair, the
-// block's interior links and three block fields in shared memory, the clover
-// blocks read through L1. FP64 (k_sap_block): one thread per site pair, the
-// block fields in shared memory, links and clover blocks from the global
-// fields.
+// FP32, single lattice: k_sap_resid computes r = eta - D psi on the sites of
+// the colour in the L2-friendly sweep order of the D kernel (skipped while
+// psi = 0, where r = eta), then k_sap_split solves the blocks: two threads per
+// site pair, the block's interior compound links W' = -1/2 z^qhat U (all three
+// rows) and two block fields in shared memory, the clover blocks read through
+// L1. FP32, batched (k_sap_block_batch): the same block solve, each thread
+// computing its site's residual itself. FP64 (k_sap_block): one thread per
+// site pair, the block fields in shared memory, links and clover blocks from
+// the global fields.
 #include <algorithm>
 #include <vector>
 
@@ -339,46 +343,46 @@ __global__ void __launch_bounds__(SAP_THREADS, 2) k_sap_block(Geom g, SapGeom sg
 // (mu = 1, 2). The partner's share is exchanged once per hop set with a warp
 // shuffle. The clover term acts within a chirality, so each thread computes
 // its three rows of both 6x6 blocks after one shuffle of the partner's half.
-// The arithmetic per block is that of the one-thread-per-pair form, except
-// that both threads of a pair rebuild each link's third row; it is spread
-// over twice the threads at about half the registers each.
+// The block's compound links W' = -1/2 z^qhat U are staged once per launch
+// with all three rows, so a hop is a projection, one 3x3 complex product and
+// the accumulation: no third-row rebuild, no U(1) phase, no factor -1/2.
 // ---------------------------------------------------------------------------
 constexpr int SPLIT_THREADS = 256;
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
-// Shared-memory fields keep the [24][128] layout of SmemField, with the
-// slots of spins 1 and 3 rotated by 16: the two threads of a pair read the
-// same slot in spins of opposite parity, which then fall in different banks.
-__device__ __forceinline__ const float* spin_ptr(const float* a, int spin, int slot) {
-    return a + 6 * spin * SAP_HALF + ((slot + 16 * (spin & 1)) & (SAP_HALF - 1));
-}
-__device__ __forceinline__ void ld_spin(const float* a, int spin, int slot, cplx<float> v[3]) {
-    const float* p = spin_ptr(a, spin, slot);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) v[c] = mk(p[(2 * c) * SAP_HALF], p[(2 * c + 1) * SAP_HALF]);
-}
-__device__ __forceinline__ void st_spin(float* a, int spin, int slot, const cplx<float> v[3]) {
-    float* p = const_cast<float*>(spin_ptr(a, spin, slot));
+// Shared-memory block fields of the split kernel: float2 [12][128], entry
+// (3 spin + colour, pair slot) a complex number, with the slots of spins 1
+// and 3 rotated by 8. The two threads of a pair read the same slot in spins
+// of opposite parity; the rotation puts the eight pairs of a half warp on
+// disjoint halves of the 32 banks.
+__device__ __forceinline__ int spin_slot(int spin, int slot) { return (slot + 8 * (spin & 1)) & (SAP_HALF - 1); }
+__device__ __forceinline__ void ld_spin(const float2* a, int spin, int slot, cplx<float> v[3]) {
+    const float2* p = a + 3 * spin * SAP_HALF + spin_slot(spin, slot);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        p[(2 * c) * SAP_HALF] = v[c].re;
-        p[(2 * c + 1) * SAP_HALF] = v[c].im;
+        const float2 x = p[c * SAP_HALF];
+        v[c] = mk(x.x, x.y);
     }
 }
+__device__ __forceinline__ void st_spin(float2* a, int spin, int slot, const cplx<float> v[3]) {
+    float2* p = a + 3 * spin * SAP_HALF + spin_slot(spin, slot);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p[c * SAP_HALF] = make_float2(v[c].re, v[c].im);
+}
 // own half: v[0..2] spin sg, v[3..5] spin 2 + sg
-__device__ __forceinline__ void ld_half(const float* a, int sg, int slot, cplx<float> v[6]) {
+__device__ __forceinline__ void ld_half(const float2* a, int sg, int slot, cplx<float> v[6]) {
     ld_spin(a, sg, slot, v);
     ld_spin(a, 2 + sg, slot, v + 3);
 }
-__device__ __forceinline__ void st_half(float* a, int sg, int slot, const cplx<float> v[6]) {
+__device__ __forceinline__ void st_half(float2* a, int sg, int slot, const cplx<float> v[6]) {
     st_spin(a, sg, slot, v);
     st_spin(a, 2 + sg, slot, v + 3);
 }
-__device__ __forceinline__ void ld_full(const float* a, int slot, cplx<float> v[12]) {
+__device__ __forceinline__ void ld_full(const float2* a, int slot, cplx<float> v[12]) {
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp) ld_spin(a, sp, slot, v + 3 * sp);
 }
-__device__ __forceinline__ void st_full(float* a, int slot, const cplx<float> v[12]) {
+__device__ __forceinline__ void st_full(float2* a, int slot, const cplx<float> v[12]) {
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp) st_spin(a, sp, slot, v + 3 * sp);
 }
@@ -405,30 +409,34 @@ __device__ __forceinline__ int link_entry(int p, int lidx) {
     }
 }
 
+// Compound block links of the split kernel, W'(x,mu) = -1/2 z(x,mu)^qhat
+// U(x,mu), all three rows, staged once per launch so that the hops need
+// neither the third-row reconstruction nor the U(1) phase nor the factor
+// -1/2. Entry e of direction mu: float4 W4[mu][k][e], k = 0..3, holds the
+// complex entries (00, 01), (02, 10), (11, 12), (20, 21); float2 W2[mu][e]
+// holds (22).
 struct SplitLinks {
-    const float4* U;  // [4][3][192] two rows
-    const float2* Z;  // [4][192] z^qhat
+    const float4* W4;  // [4][4][192]
+    const float2* W2;  // [4][192]
     __device__ __forceinline__ void link(int mu, int e, cplx<float> u[3][3]) const {
-        const float4 a = U[(mu * 3 + 0) * SPLIT_LINKS + e];
-        const float4 b = U[(mu * 3 + 1) * SPLIT_LINKS + e];
-        const float4 c = U[(mu * 3 + 2) * SPLIT_LINKS + e];
+        const float4 a = W4[(mu * 4 + 0) * SPLIT_LINKS + e];
+        const float4 b = W4[(mu * 4 + 1) * SPLIT_LINKS + e];
+        const float4 c = W4[(mu * 4 + 2) * SPLIT_LINKS + e];
+        const float4 d = W4[(mu * 4 + 3) * SPLIT_LINKS + e];
+        const float2 z = W2[mu * SPLIT_LINKS + e];
         u[0][0] = mk(a.x, a.y);
         u[0][1] = mk(a.z, a.w);
         u[0][2] = mk(b.x, b.y);
         u[1][0] = mk(b.z, b.w);
         u[1][1] = mk(c.x, c.y);
         u[1][2] = mk(c.z, c.w);
-        u[2][0] = conj(u[0][1] * u[1][2] - u[0][2] * u[1][1]);
-        u[2][1] = conj(u[0][2] * u[1][0] - u[0][0] * u[1][2]);
-        u[2][2] = conj(u[0][0] * u[1][1] - u[0][1] * u[1][0]);
-    }
-    __device__ __forceinline__ cplx<float> phase(int mu, int e) const {
-        const float2 z = Z[mu * SPLIT_LINKS + e];
-        return mk(z.x, z.y);
+        u[2][0] = mk(d.x, d.y);
+        u[2][1] = mk(d.z, d.w);
+        u[2][2] = mk(z.x, z.y);
     }
 };
 
-constexpr size_t split_link_bytes() { return 12 * SPLIT_LINKS * sizeof(float4) + 4 * SPLIT_LINKS * sizeof(float2); }
+constexpr size_t split_link_bytes() { return 16 * SPLIT_LINKS * sizeof(float4) + 4 * SPLIT_LINKS * sizeof(float2); }
 
 // Hops of direction MU inside the block for thread sg (sgn = +1 for sg = 0,
 // -1 for sg = 1). With a the neighbour's spin sg and b the lower spin named
@@ -437,7 +445,7 @@ constexpr size_t split_link_bytes() { return 12 * SPLIT_LINKS * sizeof(float4) +
 // DIR, 1 / -i / sgn / -sgn i for MU = 0..3, to al (lower spin 2 + sg, MU =
 // 0, 3) or ax (lower spin 3 - sg, the partner's, MU = 1, 2).
 template <bool QNZ, int MU>
-__device__ __forceinline__ void split_dir(const SplitLinks& bl, const float* src, const Site& t, int p, int sg,
+__device__ __forceinline__ void split_dir(const SplitLinks& bl, const float2* src, const Site& t, int p, int sg,
                                           float sgn, cplx<float> au[3], cplx<float> al[3], cplx<float> ax[3]) {
     constexpr int stride = MU == 0 ? 64 : MU == 1 ? 16 : MU == 2 ? 4 : 1;
     const int lspin = (MU == 0 || MU == 3) ? 2 + sg : 3 - sg;
@@ -456,7 +464,6 @@ __device__ __forceinline__ void split_dir(const SplitLinks& bl, const float* src
         const int e = link_entry<MU>(p, t.lidx);
         bl.link(MU, e, u);
         su3_mul(u, h, gv);
-        if (QNZ) times3(bl.phase(MU, e), gv);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             au[c] = au[c] + gv[c];
@@ -480,7 +487,6 @@ __device__ __forceinline__ void split_dir(const SplitLinks& bl, const float* src
         const int e = link_entry<MU>(1 - p, t.lidx - stride);  // link of the neighbour (other parity)
         bl.link(MU, e, u);
         su3_dag_mul(u, h, gv);
-        if (QNZ) times3(conj(bl.phase(MU, e)), gv);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             au[c] = au[c] + gv[c];
@@ -496,7 +502,7 @@ __device__ __forceinline__ void split_dir(const SplitLinks& bl, const float* src
 // every thread of the warp must call it (one shuffle at the end)
 // (site t of parity p)
 template <bool QNZ>
-__device__ __forceinline__ void split_hops(const SplitLinks& bl, const float* src, const Site& t, int p, int sg,
+__device__ __forceinline__ void split_hops(const SplitLinks& bl, const float2* src, const Site& t, int p, int sg,
                                            float sgn, cplx<float> acc[6]) {
     cplx<float> au[3], al[3], ax[3];
 #pragma unroll
@@ -561,19 +567,22 @@ __device__ __forceinline__ void clover_half(const float4* __restrict__ C, int V,
 
 // Same phases as sap_block_body, with the site-pair work split over the
 // two threads of a pair. The residual is computed one site per thread.
-template <bool QNZ>
+// RIN: the residual r = eta - D psi of the blocks is read from rin (computed
+// by k_sap_resid over the whole colour, or eta itself while psi = 0);
+// otherwise every thread computes the residual of its site here.
+template <bool QNZ, bool RIN>
 __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm, int bidx, int colour, int psi_zero,
                                                const Fields<float>& f, const float4* __restrict__ Cinv,
-                                               const float4* __restrict__ eta, int nmr, float q) {
+                                               const float4* __restrict__ eta, const float4* __restrict__ rin,
+                                               int nmr, float q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4* sU = reinterpret_cast<float4*>(smem_raw);
-    float2* sZ = reinterpret_cast<float2*>(smem_raw + 12 * SPLIT_LINKS * sizeof(float4));
-    const SplitLinks bl{sU, sZ};
-    float* sm = reinterpret_cast<float*>(smem_raw + split_link_bytes());
-    float* s_ro = sm;                   // r on the odd sites, then delta_o
-    float* s_rho = sm + 24 * SAP_HALF;  // r on the even sites, then the MR residual
-    float* s_t = sm + 48 * SAP_HALF;    // odd temporary / delta_e at the end
-    float* red = sm + 72 * SAP_HALF;    // 3 * warps reduction slots
+    float4* sW4 = reinterpret_cast<float4*>(smem_raw);
+    float2* sW2 = reinterpret_cast<float2*>(smem_raw + 16 * SPLIT_LINKS * sizeof(float4));
+    const SplitLinks bl{sW4, sW2};
+    float2* sm = reinterpret_cast<float2*>(smem_raw + split_link_bytes());
+    float2* s_rho = sm;                 // r on the even sites, the MR residual, delta_o at the end
+    float2* s_t = sm + 12 * SAP_HALF;   // r on the odd sites, the odd temporary, delta_e at the end
+    float* red = reinterpret_cast<float*>(sm + 24 * SAP_HALF);  // 3 * warps reduction slots
 
     // blocks (b0, b1, b2, b3e) and (.., b3e + 1), b3e even: one of each colour
     int org[4], org3_other;
@@ -612,7 +621,8 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
         for (int k = 0; k < 6; ++k) pz[(size_t)k * g.V + z.s] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
-    // interior links of this thread's site (se has parity 0, so parity 1)
+    // compound links W' = -1/2 z^qhat U of this thread's site that stay
+    // inside the block (se has parity 0, so parity sg)
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
         if (me.l[mu] == SAP_BS - 1) continue;
@@ -620,22 +630,34 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
                       : mu == 1 ? link_entry<1>(sg, me.lidx)
                       : mu == 2 ? link_entry<2>(sg, me.lidx)
                                 : link_entry<3>(sg, me.lidx);
+        cplx<float> u[3][3];
+        load_link(f.U, g.V, mu, me.s, u);
+        cplx<float> z = QNZ ? link_phase(f.A, g.V, mu, me.s, q) : mk(1.f, 0.f);
+        z = -0.5f * z;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) sU[(mu * 3 + j) * SPLIT_LINKS + e] = f.U[((size_t)mu * 3 + j) * g.V + me.s];
-        const cplx<float> z = QNZ ? link_phase(f.A, g.V, mu, me.s, q) : mk(1.f, 0.f);
-        sZ[mu * SPLIT_LINKS + e] = make_float2(z.re, z.im);
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) u[a][b] = z * u[a][b];
+        sW4[(mu * 4 + 0) * SPLIT_LINKS + e] = make_float4(u[0][0].re, u[0][0].im, u[0][1].re, u[0][1].im);
+        sW4[(mu * 4 + 1) * SPLIT_LINKS + e] = make_float4(u[0][2].re, u[0][2].im, u[1][0].re, u[1][0].im);
+        sW4[(mu * 4 + 2) * SPLIT_LINKS + e] = make_float4(u[1][1].re, u[1][1].im, u[1][2].re, u[1][2].im);
+        sW4[(mu * 4 + 3) * SPLIT_LINKS + e] = make_float4(u[2][0].re, u[2][0].im, u[2][1].re, u[2][1].im);
+        sW2[mu * SPLIT_LINKS + e] = make_float2(u[2][2].re, u[2][2].im);
     }
 
     {
         cplx<float> r[12];
-        residual_body<float, QNZ>(g, f, eta, q, me, psi_zero, r);
-        st_full(sg ? s_ro : s_rho, t, r);
+        if (RIN) load_spinor(rin, g.V, me.s, r);
+        else residual_body<float, QNZ>(g, f, eta, q, me, psi_zero, r);
+        st_full(sg ? s_t : s_rho, t, r);
     }
     __syncthreads();
 
-    cplx<float> v[6], w[6], acc[6], rho[6];
-    ld_half(s_ro, sg, t, v);
-    clover_half(Cinv, g.V, so.s, sg, sgn, v, w);  // t_o = M_oo^-1 r_o
+    // r_o (this thread's half) stays in registers until the last step; the
+    // pair overwrites its own halves of s_t with t_o = M_oo^-1 r_o
+    cplx<float> ro[6], v[6], w[6], acc[6], rho[6];
+    ld_half(s_t, sg, t, ro);
+    clover_half(Cinv, g.V, so.s, sg, sgn, ro, w);
     st_half(s_t, sg, t, w);
     __syncthreads();
 
@@ -649,27 +671,25 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
         const bool odd = (step & 1) != 0;
         const bool last = step == nsteps - 1;
         split_hops<QNZ>(bl, odd ? (last ? s_t : s_rho) : s_t, odd ? so : se, odd ? 1 : 0, sg, sgn, acc);
+        // acc = H psi on the sites of this step's parity (the links carry the -1/2)
         if (step == 0) {
             ld_half(s_rho, sg, t, rho);  // r_e
 #pragma unroll
-            for (int i = 0; i < 6; ++i) rho[i] = rho[i] + 0.5f * acc[i];
+            for (int i = 0; i < 6; ++i) rho[i] = rho[i] - acc[i];
             st_half(s_rho, sg, t, rho);
         } else if (last) {
-            ld_half(s_ro, sg, t, v);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) v[i] = v[i] + 0.5f * acc[i];
-            clover_half(Cinv, g.V, so.s, sg, sgn, v, w);  // delta_o
-            st_half(s_ro, sg, t, w);
+            for (int i = 0; i < 6; ++i) v[i] = ro[i] - acc[i];
+            clover_half(Cinv, g.V, so.s, sg, sgn, v, w);  // delta_o (s_rho is no longer read)
+            st_half(s_rho, sg, t, w);
         } else if (odd) {
-#pragma unroll
-            for (int i = 0; i < 6; ++i) v[i] = -0.5f * acc[i];
-            clover_half(Cinv, g.V, so.s, sg, sgn, v, w);
+            clover_half(Cinv, g.V, so.s, sg, sgn, acc, w);
             st_half(s_t, sg, t, w);
         } else {
             ld_half(s_rho, sg, t, rho);
             clover_half(f.C, g.V, se.s, sg, sgn, rho, w);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) w[i] = w[i] + 0.5f * acc[i];
+            for (int i = 0; i < 6; ++i) w[i] = w[i] - acc[i];
             float a_re = 0.f, a_im = 0.f, b = 0.f;
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
@@ -693,9 +713,9 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
         }
         __syncthreads();
     }
-    // psi_B += delta on this thread's site: delta_e in s_t, delta_o in s_ro
+    // psi_B += delta on this thread's site: delta_e in s_t, delta_o in s_rho
     cplx<float> d[12];
-    ld_full(sg ? s_ro : s_t, t, d);
+    ld_full(sg ? s_rho : s_t, t, d);
     float4* psi = const_cast<float4*>(f.psi);
     if (!psi_zero) {
         cplx<float> o[12];
@@ -707,10 +727,13 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
 }
 
 template <bool QNZ>
-__global__ void __launch_bounds__(SPLIT_THREADS, 2) k_sap_split(Geom g, SapGeom sgm, int colour, int psi_zero,
-                                                                Fields<float> f, const float4* __restrict__ Cinv,
-                                                                const float4* __restrict__ eta, int nmr, float q) {
-    sap_split_body<QNZ>(g, sgm, blockIdx.x, colour, psi_zero, f, Cinv, eta, nmr, q);
+__global__ void __launch_bounds__(SPLIT_THREADS, 2) k_sap_split(const __grid_constant__ Geom g,
+                                                                const __grid_constant__ SapGeom sgm, int colour,
+                                                                int psi_zero, const __grid_constant__ Fields<float> f,
+                                                                const float4* __restrict__ Cinv,
+                                                                const float4* __restrict__ eta,
+                                                                const float4* __restrict__ rin, int nmr, float q) {
+    sap_split_body<QNZ, true>(g, sgm, blockIdx.x, colour, psi_zero, f, Cinv, eta, rin, nmr, q);
 }
 
 // batched form: thread block b works on block (b - cta_begin) of the job
@@ -725,13 +748,55 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 2) k_sap_block_batch(const SapJ
         else hi = mid - 1;
     }
     const SapJob& J = jobs[lo];
-    sap_split_body<true>(J.g, J.sg, b - J.cta_begin, colour, psi_zero, J.f, J.Cinv, J.eta, nmr, J.q);
+    sap_split_body<true, false>(J.g, J.sg, b - J.cta_begin, colour, psi_zero, J.f, J.Cinv, J.eta, nullptr, nmr, J.q);
+}
+
+// r = eta - D psi at the sites of the blocks of colour `colour` (the residual
+// of a Schwarz half-cycle), one thread per site, written to r in the native
+// layout. The sites are visited in the tiled sweep order of the D kernel
+// restricted to the colour: in a row of x3 the colour changes every 4 sites,
+// so entry j of the row's N3/2 sites of the colour is
+// x3 = 8 (j / 4) + 4 k + j mod 4, k = (x0/4 + x1/4 + x2/4 + colour) mod 2.
+template <bool QNZ>
+__global__ void __launch_bounds__(DW_THREADS, DW_PP_MIN_BLOCKS)
+    k_sap_resid(const __grid_constant__ Geom g, int colour, const __grid_constant__ Fields<float> f,
+                const float4* __restrict__ eta, float4* __restrict__ r, float q) {
+    const int tau = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tau >= g.Vh) return;
+    const int half3 = g.N3 >> 1;
+    const int rowlen = g.R * half3;
+    const int within = tau % rowlen;
+    int rest = tau / rowlen;
+    const int x1 = rest % g.N1;
+    rest /= g.N1;
+    const int x0 = rest % g.N0;
+    const int chunk = rest / g.N0;
+    const int row = within / half3;
+    const int j = within - row * half3;
+    const int x2 = chunk * g.R + row;
+    const int k = ((x0 >> 2) + (x1 >> 2) + (x2 >> 2) + colour) & 1;
+    const int x3 = 8 * (j >> 2) + 4 * k + (j & 3);
+    const int p = (x0 + x1 + x2 + x3) & 1;
+    const int s = native_index(g, lex_index(g, x0, x1, x2, x3), p);
+    int nb[8];
+    neighbours8(g, x0, x1, x2, x3, 1 - p, nb);
+    cplx<float> acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = mk(0.f, 0.f);
+    hops_pipelined<QNZ>(f, g.V, s, nb, q, acc);
+    cplx<float> v[12], w[12];
+    load_spinor(f.psi, g.V, s, v);
+    clover_mul<true>(f.C, g.V, s, v, w);
+    load_spinor(eta, g.V, s, v);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) v[i] = v[i] - (w[i] - 0.5f * acc[i]);
+    store_spinor_cs(r, g.V, s, v);
 }
 
 template <typename R>
 size_t sap_smem_bytes() {
-    if (sizeof(R) == 4)  // split kernel: interior links, three block fields, reduction slots of 8 warps
-        return split_link_bytes() + (72 * SAP_HALF + 3 * (SPLIT_THREADS / 32)) * sizeof(R);
+    if (sizeof(R) == 4)  // split kernel: interior compound links, two block fields, reduction slots of 8 warps
+        return split_link_bytes() + 24 * SAP_HALF * sizeof(float2) + 3 * (SPLIT_THREADS / 32) * sizeof(float);
     return (72 * SAP_HALF + 3 * (SAP_THREADS / 32)) * sizeof(R);
 }
 
@@ -758,9 +823,18 @@ int launch_sap_block(qxd_lattice* lat, const SapGeom& sg, int colour, int psi_ze
                      cudaStream_t st) {
     const size_t smem = sap_smem_bytes<R>();
     if constexpr (sizeof(R) == 4) {
+        // the residual of the colour: eta itself while psi = 0, else from k_sap_resid
+        const float4* rin = eta;
+        if (!psi_zero) {
+            const Geom& g = lat->g;
+            k_sap_resid<QNZ><<<(g.Vh + DW_THREADS - 1) / DW_THREADS, DW_THREADS, 0, st>>>(g, colour, f, eta, lat->sap_r,
+                                                                                      (float)lat->qhat);
+            QXD_LAUNCHED("k_sap_resid");
+            rin = lat->sap_r;
+        }
         int rc = split_attrs(k_sap_split<QNZ>, smem);
         if (rc) return rc;
-        k_sap_split<QNZ><<<sg.nhalf, SPLIT_THREADS, smem, st>>>(lat->g, sg, colour, psi_zero, f, Cinv, eta, nmr,
+        k_sap_split<QNZ><<<sg.nhalf, SPLIT_THREADS, smem, st>>>(lat->g, sg, colour, psi_zero, f, Cinv, eta, rin, nmr,
                                                                 (float)lat->qhat);
         QXD_LAUNCHED("k_sap_split");
     } else {
@@ -823,6 +897,13 @@ int sap_apply(qxd_lattice* lat, SapWork& w, void* out, const void* in, int ncy, 
     // without reading psi, and the blocks of colour 1 must read zeros there
     // (the FP32 kernel clears them itself in its first launch)
     if (sizeof(R) == 8) QXD_CUDA(cudaMemsetAsync(out, 0, (size_t)g.V * 24 * sizeof(R), st));
+    if (sizeof(R) == 4 && !lat->sap_r) {
+        const cudaError_t e = cudaMalloc(&lat->sap_r, (size_t)g.V * SPINOR_F4 * sizeof(float4));
+        if (e != cudaSuccess) {
+            lat->sap_r = nullptr;
+            return cuda_fail(e, "SAP: cudaMalloc(residual field)");
+        }
+    }
     int rc;
     for (int cy = 0; cy < ncy; ++cy)
         for (int colour = 0; colour < 2; ++colour) {

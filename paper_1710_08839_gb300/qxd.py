@@ -136,6 +136,11 @@ SIGNATURES = {
     "qxd_spinor_pack": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_spinor_unpack": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_fma_rate": (_i, [_i, _i, ctypes.POINTER(_d), _vp]),
+    "qxd_set_autotune": (_i, [_i]),
+    "qxd_dw_shape": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                          ctypes.POINTER(ctypes.c_float)]),
+    "qxd_dw_set_shape": (_i, [_vp, _i, _i, _i, _i]),
+    "qxd_tune_report": (_i, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "qxd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -294,6 +299,20 @@ def qxd_Dw_batch(lats, outs, ins, prec, rhs_per_site=0, stream=0) -> int:
     return check(_call("qxd_Dw_batch", n, arr(lats), arr(outs), arr(ins), prec, rhs_per_site, stream))
 
 
+def set_autotune(enable: bool) -> bool:
+    """qxd_set_autotune; returns the previous setting."""
+    return bool(lib().qxd_set_autotune(1 if enable else 0))
+
+
+def tune_report() -> str:
+    """qxd_tune_report: every launch-shape choice made so far, one per line."""
+    need = ctypes.c_size_t()
+    check(lib().qxd_tune_report(None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value + 64)
+    check(lib().qxd_tune_report(buf, len(buf), ctypes.byref(need)))
+    return buf.value.decode()
+
+
 QXD_PROBE_FMA64 = 0
 QXD_PROBE_FMA32 = 1
 QXD_PROBE_FMA32X2 = 2
@@ -395,6 +414,17 @@ class Lattice:
 
     def spinor_bytes(self, prec):
         return qxd_spinor_bytes(self.handle, prec)
+
+    def dw_shape(self, prec):
+        """qxd_dw_shape: the launch shape chosen for D on this lattice shape."""
+        pl, th, rows, ms = _i(), _i(), _i(), ctypes.c_float()
+        check(lib().qxd_dw_shape(self.handle, int(prec), ctypes.byref(pl), ctypes.byref(th), ctypes.byref(rows),
+                                 ctypes.byref(ms)))
+        return {"pipelined": bool(pl.value), "threads": th.value, "rows": rows.value, "ms": ms.value}
+
+    def set_dw_shape(self, prec, pipelined, threads, rows):
+        """qxd_dw_set_shape: pin the launch shape of D for this lattice shape."""
+        check(lib().qxd_dw_set_shape(self.handle, int(prec), int(pipelined), int(threads), int(rows)))
 
     def Dw(self, out, inp, prec=None, native=False, stream=None):
         torch = _torch()

@@ -88,3 +88,13 @@ def test_engine_entry_points_check_arguments():
     e = ctypes.c_void_p()
     assert lib.qxd_engine_create(ctypes.byref(e), 0, 0, None) == qxd.QXD_ERR_ARG
     assert lib.qxd_engine_destroy(None) == qxd.QXD_OK
+
+
+def test_tuning_entry_points_without_a_gpu():
+    lib = qxd.lib()
+    prev = lib.qxd_set_autotune(0)
+    assert lib.qxd_set_autotune(prev) == 0
+    need = ctypes.c_size_t()
+    assert lib.qxd_tune_report(None, 0, ctypes.byref(need)) == qxd.QXD_OK and need.value >= 1
+    assert lib.qxd_dw_shape(None, qxd.QXD_FP32, None, None, None, None) == qxd.QXD_ERR_ARG
+    assert lib.qxd_dw_set_shape(None, qxd.QXD_FP32, 1, 128, 2) == qxd.QXD_ERR_ARG

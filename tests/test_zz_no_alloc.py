@@ -5,6 +5,7 @@ checked to leave the device's free memory unchanged and against qxd_Dw (the
 entry point that allocates its conversion scratch); the size limit is
 checked too. Collected last on purpose."""
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -50,11 +51,19 @@ def test_noalloc_matches_Dw_on_two_calls(prec):
     warm = torch.empty_like(xs[0])
     assert _noalloc(lat, warm, xs[0], p) == qxd.QXD_OK, qxd.qxd_last_error()
     torch.cuda.synchronize()
-    free_before = torch.cuda.mem_get_info()[0]
-    for x, y in zip(xs, ys):
-        assert _noalloc(lat, y, x, p) == qxd.QXD_OK, qxd.qxd_last_error()
-    torch.cuda.synchronize()
-    assert torch.cuda.mem_get_info()[0] == free_before
+    # no Python garbage collection in the measured window: a lattice left by
+    # an earlier test and finalised there would free device memory
+    gc.collect()
+    gc.disable()
+    try:
+        free_before = torch.cuda.mem_get_info()[0]
+        for x, y in zip(xs, ys):
+            assert _noalloc(lat, y, x, p) == qxd.QXD_OK, qxd.qxd_last_error()
+        torch.cuda.synchronize()
+        free_after = torch.cuda.mem_get_info()[0]
+    finally:
+        gc.enable()
+    assert free_after == free_before, (free_before, free_after)
     for x, y in zip(xs, ys):
         ref = torch.empty_like(x)
         lat.Dw(ref, x)
