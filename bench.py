@@ -299,7 +299,9 @@ BATCH_WORKLOAD = dict(
 # resident ensemble per size, m0 ~ U[0.02, 0.2], qhat from {-1, 0, 2}
 SERVE_WORKLOAD = dict(sizes=[(8, 16), (16, 32), (24, 48), (32, 64)], probs=[0.4, 0.3, 0.2, 0.1], n=512,
                       eps=0.3, sigma=0.3, csw=1.0, cswqed=1.0, m0=(0.02, 0.2), qs=(-1, 0, 2), tol=1e-10,
-                      seed=3000, budget_gb=80, load=0.8)
+                      seed=3000, budget_gb=80, load=0.8,
+                      # serving runtime: one engine lane per size class (bounds on the simulated sites)
+                      lane_sites=[100000, 1000000, 2000000], lane_budget_gb=[4, 12, 24, 40])
 
 
 def _fp64_params(qxd):
@@ -415,7 +417,10 @@ def batch_benchmark(qxd, torch):
 
 
 def serve_benchmark(qxd, torch):
-    """Continuous batching of a Poisson request stream through the engine."""
+    """Continuous batching of a Poisson request stream: through the serving
+    runtime (one engine lane per size class, each with its own stream and
+    worker thread), and for comparison through one lockstep engine at the
+    same arrival rate."""
     import numpy as np
 
     import synth
@@ -461,11 +466,14 @@ def serve_benchmark(qxd, torch):
     # a host queue, their latency counted from arrival
     cap = w.get("inflight_cap", [64, 32, 12, 6])
     eng = qxd.Engine(hbm_budget_bytes=w["budget_gb"] << 30, max_active=256)
+    srv = qxd.Server(w["lane_sites"], [g << 30 for g in w["lane_budget_gb"]], max_active=256)
 
-    def run(arrivals):
+    def run(arrivals, server=None):
         """Serve the requests with arrival times `arrivals` (s). A preparation
         thread builds each admitted request's operator (view + clover term) and
-        source on its own stream while the main thread steps the engine."""
+        source on its own stream while the main thread submits and polls
+        (server: the lanes step themselves) or steps the lockstep engine."""
+        be = server if server is not None else eng
         from collections import deque
         todo, ready = queue.Queue(), queue.Queue()
 
@@ -505,12 +513,17 @@ def serve_benchmark(qxd, torch):
                     r, v, x, b = ready.get_nowait()
                 except queue.Empty:
                     break
-                rid = eng.submit(v, x, b, tol=w["tol"])
+                rid = be.submit(v, x, b, tol=w["tol"])
                 inflight[rid] = (r, v, x, b, arrivals[r])
-            a, p, d = eng.step()
-            if d or (a == 0 and p == 0):
+            if server is None:
+                a, p, d = eng.step()
+                check, idle = d or (a == 0 and p == 0), a == 0 and p == 0
+            else:
+                time.sleep(0.0002)
+                check, idle = True, not inflight
+            if check:
                 for rid in list(inflight):
-                    fin, info = eng.poll(rid)
+                    fin, info = be.poll(rid)
                     if fin:
                         r, v, x, b, t_arr = inflight.pop(rid)
                         if info["status"] != qxd.QXD_OK:
@@ -518,9 +531,9 @@ def serve_benchmark(qxd, torch):
                         lat_ms.append((time.perf_counter() - t0 - t_arr) * 1e3)
                         release(size_idx[r], v)
                         busy[size_idx[r]] -= 1
-                        eng.forget(rid)
+                        be.forget(rid)
                         done += 1
-            if a == 0 and p == 0:
+            if idle:
                 if ready.empty() and any(busy):
                     time.sleep(0.0005)  # the preparation thread is working
                 elif not any(busy) and nxt < n:
@@ -534,12 +547,17 @@ def serve_benchmark(qxd, torch):
     # saturated throughput (all requests at t = 0; a first pass warms the
     # view pools, allocator and autotuned kernels), then Poisson arrivals at
     # `load` times that rate
-    run(np.zeros(n))
-    t_sat, _ = run(np.zeros(n))
+    run(np.zeros(n), srv)
+    t_sat, _ = run(np.zeros(n), srv)
     rate = w["load"] * n / t_sat
     arr = np.cumsum(rng.exponential(1.0 / rate, size=n))
     arr -= arr[0]
-    t_poi, lat_ms = run(arr)
+    t_poi, lat_ms = run(arr, srv)
+    lane_stats = [srv.stats(i) for i in range(srv.nlanes)]
+    srv.close()
+    # the same stream through one lockstep engine
+    t_sat_e, _ = run(np.zeros(n))
+    t_poi_e, lat_e = run(arr)
     eng.close()
     # one-at-a-time references: the first six requests of each size timed
     # alone (operator build + solve), averaged per size
@@ -570,13 +588,20 @@ def serve_benchmark(qxd, torch):
             v.close()
     for e in ens:
         e.close()
-    p50 = lat_ms[len(lat_ms) // 2]
-    p99 = lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))]
+    def pct(v, f):
+        return v[min(len(v) - 1, int(f * len(v)))]
+
     return {
         "workload": f"{n} requests, Poisson arrivals, sizes (L,T) {w['sizes']} with p {w['probs']} (C*, doubled), "
                     "m0 ~ U[0.02,0.2], qhat in {-1,0,2}, Gaussian sources, tol 1e-10",
+        "runtime": f"qxd_server: {len(w['lane_budget_gb'])} engine lanes by simulated sites {w['lane_sites']}, "
+                   f"budgets {w['lane_budget_gb']} GB, each with its own stream and worker thread",
         "saturated_solves_per_s": n / t_sat, "arrival_rate_per_s": rate,
-        "poisson_solves_per_s": n / t_poi, "p50_latency_ms": p50, "p99_latency_ms": p99,
+        "poisson_solves_per_s": n / t_poi, "p50_latency_ms": pct(lat_ms, 0.5), "p99_latency_ms": pct(lat_ms, 0.99),
+        "lanes": lane_stats,
+        "lockstep_engine": {"saturated_solves_per_s": n / t_sat_e, "poisson_solves_per_s": n / t_poi_e,
+                            "p50_latency_ms": pct(lat_e, 0.5), "p99_latency_ms": pct(lat_e, 0.99),
+                            "note": "one qxd_engine stepping every request in lockstep, same arrivals"},
         "one_at_a_time_fp64_solves_per_s_est": n / seq64, "one_at_a_time_mixed_solves_per_s_est": n / seqmix,
         "speedup_saturated_vs_fp64_one_at_a_time": seq64 / t_sat,
         "counts_per_size": counts.tolist(),

@@ -340,6 +340,37 @@ int qxd_engine_stats(const qxd_engine* e, size_t* bytes_in_use, size_t* bytes_he
 int qxd_engine_graph_stats(const qxd_engine* e, long long* captures, long long* replays);
 
 /* ---------------------------------------------------------------------------
+ * Serving runtime: lanes of the solve engine by lattice size. The paper has
+ * no counterpart. Lane i takes the requests on lattices of fewer than
+ * lane_sites[i] simulated sites (not taken by an earlier lane; the last lane
+ * takes the rest) and has its own CUDA stream, its own engine
+ * (qxd_engine_create with lane_budget[i] bytes and max_active) and its own
+ * host worker thread, which admits, steps and retires that lane's requests
+ * without waiting for the other lanes: a request on a small lattice does not
+ * wait for the steps of large ones. A request's result is the engine's (the
+ * same, bit for bit, as the request solved alone). submit, poll, forget and
+ * stats may be called from any thread. Buffers x and b and the operator must
+ * stay valid and unchanged until the request is done. qxd_server_destroy
+ * waits until every submitted request is done, then stops the workers.
+ * ------------------------------------------------------------------------- */
+typedef struct qxd_server qxd_server;
+
+/* nlanes >= 1; lane_sites: nlanes - 1 positive increasing bounds (may be
+ * NULL if nlanes = 1); lane_budget: nlanes byte budgets; max_active >= 1 */
+int qxd_server_create(qxd_server** out, int nlanes, const long long* lane_sites, const size_t* lane_budget,
+                      int max_active);
+int qxd_server_destroy(qxd_server* s);
+/* queue a request (checked as by qxd_engine_submit); id receives its handle */
+int qxd_server_submit(qxd_server* s, qxd_lattice* op, void* x, const void* b, const qxd_solver_params* params,
+                      long long* id);
+/* done = 1 once x is written; info.status as for qxd_engine_poll */
+int qxd_server_poll(qxd_server* s, long long id, qxd_solve_info* info, int* done);
+/* drop the record of a finished request */
+int qxd_server_forget(qxd_server* s, long long id);
+/* requests submitted to and completed by lane `lane`, and its engine steps */
+int qxd_server_stats(const qxd_server* s, int lane, long long* submitted, long long* completed, long long* steps);
+
+/* ---------------------------------------------------------------------------
  * Pseudofermion action of the RHMC (Sec. 2.4):
  *   S_pf = -1/2 ln|Det D_oo| + sum_k phi_k^dag P_k phi_k,
  *   P_k  = prod_j (D_hat^dag D_hat + nu_j^2) / (D_hat^dag D_hat + mu_j^2),

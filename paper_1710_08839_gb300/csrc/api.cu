@@ -45,6 +45,7 @@ static int dalloc(T** p, size_t n, const char* what) {
 }
 
 static void free_all(qxd_lattice* L) {
+    release_hostio(L);
     void* own[] = {L->Zq64, L->C64, L->C32, L->Cinv64, L->Cinv32, L->d_status, L->scratch_in, L->scratch_out,
                    L->scratch_lex, L->sap_r};
     for (void* p : own)
@@ -315,18 +316,25 @@ int qxd_Dw(qxd_lattice* lat, void* out, const void* in, int flags, void* stream)
     size_t bytes = qxd_spinor_bytes(lat, prec);
     const void* lex_in = in;
     if (host) {
-        // page-locked buffers are read and written by the kernels directly;
+        // page-locked buffers are read and written by the kernels directly,
+        // pipelined over slabs of x0 planes when both are page-locked;
         // pageable ones go through a device staging copy
         void* in_dev = nullptr;
         void* out_dev = nullptr;
-        if (host_device_view(in, &in_dev)) {
+        const bool in_pl = host_device_view(in, &in_dev), out_pl = host_device_view(out, &out_dev);
+        if (in_pl && out_pl && pick_slabs(lat->g.N0) >= 3) {
+            if ((rc = dw_host_pipelined(lat, out_dev, in_dev, prec, st))) return rc;
+            QXD_CUDA(cudaStreamSynchronize(st));
+            return QXD_OK;
+        }
+        if (in_pl) {
             if ((rc = launch_pack_from_host(lat, lat->scratch_in, in_dev, prec, st))) return rc;
         } else {
             QXD_CUDA(cudaMemcpyAsync(lat->scratch_lex, in, bytes, cudaMemcpyHostToDevice, st));
             if ((rc = launch_pack(lat, lat->scratch_in, lat->scratch_lex, prec, st))) return rc;
         }
         if ((rc = launch_dirac(lat, lat->scratch_out, lat->scratch_in, prec, st))) return rc;
-        if (host_device_view(out, &out_dev)) {
+        if (out_pl) {
             if ((rc = launch_unpack_to_host(lat, out_dev, lat->scratch_out, prec, st))) return rc;
         } else {
             if ((rc = launch_unpack(lat, lat->scratch_lex, lat->scratch_out, prec, st))) return rc;

@@ -17,6 +17,11 @@
 //   A_{b,b+-mu} directly and A_{b,b} = <phi_{b,k}, T>_b - sum of the faces.
 // * Preconditioner: M eta = chi + M_SAP(eta - D chi), chi = P A^-1 P^dag eta,
 //   with the little system solved by GCR to a relative residual dfl_tol.
+//   The little GCR runs on the device: every coefficient (Gram-Schmidt
+//   projections, norms, step lengths) goes from the reduction that makes it
+//   to the kernels that use it through device memory, a restart cycle of
+//   DFL_NKV steps is one CUDA graph, and the host reads the solver state
+//   once per cycle.
 #include <chrono>
 #include <cmath>
 #include <string>
@@ -328,27 +333,6 @@ __global__ void __launch_bounds__(BSITES) k_dfl_prolong(Geom g, DflGeom d, int n
     store_spinor(out, g.V, s, w);
 }
 
-// out[b][k] = sum_j sum_l A[b][j][k][l] in[n_j(b)][l]; one thread per (b, k)
-__global__ void k_dfl_little_apply(Geom g, DflGeom d, int ns, const float2* __restrict__ A,
-                                   const double2* __restrict__ in, double2* __restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= d.nblk * ns) return;
-    const int b = i / ns, k = i - b * ns;
-    double re = 0.0, im = 0.0;
-    for (int j = 0; j < 9; ++j) {
-        const int nb = j == 0 ? b : block_nbr(g, d, b, (j - 1) >> 1, (j & 1) ? +1 : -1);
-        const float2* a = A + (((size_t)b * 9 + j) * ns + k) * ns;
-        const double2* v = in + (size_t)nb * ns;
-        for (int l = 0; l < ns; ++l) {
-            const float2 al = a[l];
-            const double2 vl = v[l];
-            re += (double)al.x * vl.x - (double)al.y * vl.y;
-            im += (double)al.x * vl.y + (double)al.y * vl.x;
-        }
-    }
-    out[i] = make_double2(re, im);
-}
-
 __global__ void k_f32_to_f64_native(int V, const float4* __restrict__ in, double2* __restrict__ out) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= V) return;
@@ -372,9 +356,16 @@ int dalloc_bytes(void** p, size_t bytes, const char* what) {
 }  // namespace
 
 void DflWork::release() {
-    void* ps[] = {basis, A, chi, tfield, H, lx, lr, lc, d_bad};
+    if (cycle) cudaGraphExecDestroy(cycle);
+    if (cap) cudaStreamDestroy(cap);
+    if (h_lstate) cudaFreeHost(h_lstate);
+    cycle = nullptr;
+    cap = nullptr;
+    h_lstate = nullptr;
+    void* ps[] = {basis, A, chi, tfield, H, lx, lr, lc, d_bad, lstate};
     for (void* p : ps)
         if (p) cudaFree(p);
+    lstate = nullptr;
     for (int k = 0; k < DFL_NKV; ++k) {
         if (lp[k]) cudaFree(lp[k]);
         if (lq[k]) cudaFree(lq[k]);
@@ -409,8 +400,10 @@ int DflWork::ensure(const Geom& g, int ns_) {
         (rc = dalloc_bytes((void**)&lx, nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
         (rc = dalloc_bytes((void**)&lr, nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
         (rc = dalloc_bytes((void**)&lc, nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
-        (rc = dalloc_bytes((void**)&d_bad, sizeof(int), "cudaMalloc(deflation status)")))
+        (rc = dalloc_bytes((void**)&d_bad, sizeof(int), "cudaMalloc(deflation status)")) ||
+        (rc = dalloc_bytes((void**)&lstate, sizeof(LittleState), "cudaMalloc(little solver state)")))
         return rc;
+    QXD_CUDA(cudaMallocHost(&h_lstate, sizeof(LittleState)));
     for (int k = 0; k < DFL_NKV; ++k)
         if ((rc = dalloc_bytes((void**)&lp[k], nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
             (rc = dalloc_bytes((void**)&lq[k], nl * sizeof(double2), "cudaMalloc(little vectors)")))
@@ -461,10 +454,274 @@ int build_little(qxd_lattice* lat, DflWork& W, cudaStream_t st) {
     return QXD_OK;
 }
 
-int little_apply(qxd_lattice* lat, DflWork& W, double2* out, const double2* in, cudaStream_t st) {
-    const int n = W.d.nblk * W.ns;
-    k_dfl_little_apply<<<(n + 127) / 128, 128, 0, st>>>(lat->g, W.d, W.ns, W.A, in, out);
-    QXD_LAUNCHED("k_dfl_little_apply");
+// ---------------------------------------------------------------------------
+// Little GCR on the device. One step k of a restart cycle is five kernels:
+//   apply:     p_k = r, q_k = A r
+//   mdot:      a_j = <q_j, q_k>, j < k                      (k > 0)
+//   orth:      q_k -= sum a_j q_j, p_k -= sum a_j p_j; qq = |q_k|^2
+//   scale_dot: q_k, p_k *= 1/sqrt(qq); al = <q_k, r>
+//   update:    x += al p_k, r -= al q_k; rn2 = |r|^2; stop when rn2 <= tol^2 |c|^2
+// The reductions write per-block partial sums; the last block to arrive
+// (counted with an atomic) adds them in block order, so each coefficient is
+// the same on every run, and stores it in the LittleState. Every kernel
+// returns at once when the state says done.
+// ---------------------------------------------------------------------------
+
+// after block_reduce_store: the last block to arrive sums the nc partials
+// in block order into out[0..nc) and returns true (in thread 0 only)
+__device__ __forceinline__ bool last_block_finish(const double* __restrict__ partials, int nc, double* out,
+                                                  unsigned* count) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    if (threadIdx.x < nc) {
+        double x = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) x += __ldcg(partials + (size_t)b * 2 * BLAS_KMAX + threadIdx.x);
+        out[threadIdx.x] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *count = 0u;
+    return threadIdx.x == 0;
+}
+
+// q = A r: q[b][k] = sum_j sum_l A[b][j][k][l] r[n_j(b)][l], one thread per
+// (b, k); also p = r. The little operator is stored in FP32 and the products
+// are taken and summed in FP32: the little system is solved only to a
+// relative residual of dfl_tol (1e-2 by default) as a preconditioner inside
+// the flexible GCR, and GB300's FP64 rate (1/63 of FP32) made the FP64 form
+// of this product the cost of a little step.
+__global__ void k_lt_apply(Geom g, DflGeom d, int ns, const float2* __restrict__ A, const double2* __restrict__ r,
+                           double2* __restrict__ p, double2* __restrict__ q, const LittleState* __restrict__ S) {
+    if (S->done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= d.nblk * ns) return;
+    const int b = i / ns, k = i - b * ns;
+    float re = 0.f, im = 0.f;
+    for (int j = 0; j < 9; ++j) {
+        const int nb = j == 0 ? b : block_nbr(g, d, b, (j - 1) >> 1, (j & 1) ? +1 : -1);
+        const float2* a = A + (((size_t)b * 9 + j) * ns + k) * ns;
+        const double2* v = r + (size_t)nb * ns;
+        for (int l = 0; l < ns; ++l) {
+            const float2 al = a[l];
+            const double2 vd = v[l];
+            const float vx = (float)vd.x, vy = (float)vd.y;
+            re = fmaf(al.x, vx, fmaf(-al.y, vy, re));
+            im = fmaf(al.x, vy, fmaf(al.y, vx, im));
+        }
+    }
+    q[i] = make_double2(re, im);
+    p[i] = r[i];
+}
+
+// the same product with coalesced reads of A, for ns = 8, 16 or 32: one warp
+// per block b; G = 32 / ns lanes share a row k, lane g of a row taking the
+// ns / G entries l in [g ns / G, (g + 1) ns / G), so that a warp reads
+// whole consecutive rows of A[b][j]; the G partial sums of a row are added
+// by warp shuffles
+template <int NS>
+__global__ void __launch_bounds__(32) k_lt_apply_warp(Geom g, DflGeom d, const float2* __restrict__ A,
+                                                      const double2* __restrict__ r, double2* __restrict__ p,
+                                                      double2* __restrict__ q, const LittleState* __restrict__ S) {
+    if (S->done) return;
+    constexpr int G = 32 / NS, CH = NS / G;
+    const int b = blockIdx.x, lane = threadIdx.x;
+    const int k = lane / G, part = lane % G;
+    float re = 0.f, im = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < 9; ++j) {
+        const int nb = j == 0 ? b : block_nbr(g, d, b, (j - 1) >> 1, (j & 1) ? +1 : -1);
+        const float2* a = A + (((size_t)b * 9 + j) * NS + k) * NS + part * CH;
+        const double2* v = r + (size_t)nb * NS + part * CH;
+#pragma unroll
+        for (int l = 0; l < CH; ++l) {
+            const float2 al = a[l];
+            const double2 vd = v[l];
+            const float vx = (float)vd.x, vy = (float)vd.y;
+            re = fmaf(al.x, vx, fmaf(-al.y, vy, re));
+            im = fmaf(al.x, vy, fmaf(al.y, vx, im));
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (part == 0) {
+        const size_t i = (size_t)b * NS + k;
+        q[i] = make_double2(re, im);
+        p[i] = r[i];
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS) k_lt_mdot(size_t n, VecList<double2> qs,
+                                                         const double2* __restrict__ qk, double* partials,
+                                                         LittleState* S) {
+    if (S->done) return;
+    constexpr int k = K;
+    double v[2 * K];
+#pragma unroll
+    for (int c = 0; c < 2 * k; ++c) v[c] = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 y = qk[i];
+#pragma unroll
+        for (int j = 0; j < k; ++j) {
+            const double2 x = qs.p[j][i];
+            v[2 * j] += x.x * y.x + x.y * y.y;
+            v[2 * j + 1] += x.x * y.y - x.y * y.x;
+        }
+    }
+    block_reduce_store<2 * K>(v, 2 * k, partials);
+    last_block_finish(partials, 2 * k, S->a, &S->count);
+}
+
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS) k_lt_orth(size_t n, VecList<double2> qs, VecList<double2> ps,
+                                                         double2* __restrict__ qk, double2* __restrict__ pk,
+                                                         double* partials, LittleState* S) {
+    if (S->done) return;
+    constexpr int k = K;
+    double a[2 * K + 1];
+#pragma unroll
+    for (int c = 0; c < 2 * k; ++c) a[c] = S->a[c];
+    double v[1] = {0.0};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double2 y = qk[i], z = pk[i];
+#pragma unroll
+        for (int j = 0; j < k; ++j) {
+            const double ar = a[2 * j], ai = a[2 * j + 1];
+            const double2 x = qs.p[j][i], w = ps.p[j][i];
+            y.x -= ar * x.x - ai * x.y;
+            y.y -= ar * x.y + ai * x.x;
+            z.x -= ar * w.x - ai * w.y;
+            z.y -= ar * w.y + ai * w.x;
+        }
+        qk[i] = y;
+        if (k > 0) pk[i] = z;
+        v[0] += y.x * y.x + y.y * y.y;
+    }
+    block_reduce_store<1>(v, 1, partials);
+    double qq;
+    if (last_block_finish(partials, 1, &qq, &S->count)) {
+        S->qq = qq;
+        if (!(qq > 0.0) || !isfinite(qq)) {
+            S->status = 1;
+            S->done = 1;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_lt_scale_dot(size_t n, double2* __restrict__ qk,
+                                                              double2* __restrict__ pk, const double2* __restrict__ r,
+                                                              double* partials, LittleState* S) {
+    if (S->done) return;
+    const double sc = 1.0 / sqrt(S->qq);
+    double v[2] = {0.0, 0.0};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double2 x = qk[i], w = pk[i];
+        x.x *= sc;
+        x.y *= sc;
+        w.x *= sc;
+        w.y *= sc;
+        qk[i] = x;
+        pk[i] = w;
+        const double2 y = r[i];
+        v[0] += x.x * y.x + x.y * y.y;
+        v[1] += x.x * y.y - x.y * y.x;
+    }
+    block_reduce_store<2>(v, 2, partials);
+    last_block_finish(partials, 2, S->al, &S->count);
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_lt_update(size_t n, const double2* __restrict__ pk,
+                                                           const double2* __restrict__ qk, double2* __restrict__ x,
+                                                           double2* __restrict__ r, double* partials, LittleState* S) {
+    if (S->done) return;
+    const double ar = S->al[0], ai = S->al[1];
+    double v[1] = {0.0};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 p = pk[i], q = qk[i];
+        double2 xi = x[i], ri = r[i];
+        xi.x += ar * p.x - ai * p.y;
+        xi.y += ar * p.y + ai * p.x;
+        ri.x -= ar * q.x - ai * q.y;
+        ri.y -= ar * q.y + ai * q.x;
+        x[i] = xi;
+        r[i] = ri;
+        v[0] += ri.x * ri.x + ri.y * ri.y;
+    }
+    block_reduce_store<1>(v, 1, partials);
+    double rn2;
+    if (last_block_finish(partials, 1, &rn2, &S->count)) {
+        S->rn2 = rn2;
+        S->it += 1;
+        if (!isfinite(rn2)) {
+            S->status = 1;
+            S->done = 1;
+        } else if (rn2 <= S->target2 || S->it >= S->max_iter) {
+            S->done = 1;
+        }
+    }
+}
+
+// the launches of one restart cycle (steps k = 0 .. DFL_NKV - 1)
+void little_cycle(qxd_lattice* lat, DflWork& W, cudaStream_t st) {
+    const size_t n = (size_t)W.d.nblk * W.ns;
+    for (int k = 0; k < DFL_NKV; ++k) {
+        if (W.ns == 16)
+            k_lt_apply_warp<16><<<W.d.nblk, 32, 0, st>>>(lat->g, W.d, W.A, W.lr, W.lp[k], W.lq[k], W.lstate);
+        else if (W.ns == 8)
+            k_lt_apply_warp<8><<<W.d.nblk, 32, 0, st>>>(lat->g, W.d, W.A, W.lr, W.lp[k], W.lq[k], W.lstate);
+        else if (W.ns == 32)
+            k_lt_apply_warp<32><<<W.d.nblk, 32, 0, st>>>(lat->g, W.d, W.A, W.lr, W.lp[k], W.lq[k], W.lstate);
+        else
+            k_lt_apply<<<(int)((n + 127) / 128), 128, 0, st>>>(lat->g, W.d, W.ns, W.A, W.lr, W.lp[k], W.lq[k],
+                                                             W.lstate);
+        VecList<double2> qs{}, ps{};
+        for (int j = 0; j < k; ++j) {
+            qs.p[j] = W.lq[j];
+            ps.p[j] = W.lp[j];
+        }
+        switch (k) {
+#define QXD_LT_GS(K)                                                                                         \
+    case K:                                                                                                   \
+        if (K > 0) k_lt_mdot<(K > 0 ? K : 1)><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, qs, W.lq[k], W.red.partials, \
+                                                                                  W.lstate);                  \
+        k_lt_orth<K><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, qs, ps, W.lq[k], W.lp[k], W.red.partials, W.lstate); \
+        break;
+            QXD_LT_GS(0) QXD_LT_GS(1) QXD_LT_GS(2) QXD_LT_GS(3) QXD_LT_GS(4) QXD_LT_GS(5) QXD_LT_GS(6)
+            QXD_LT_GS(7) QXD_LT_GS(8) QXD_LT_GS(9) QXD_LT_GS(10) QXD_LT_GS(11) QXD_LT_GS(12) QXD_LT_GS(13)
+            QXD_LT_GS(14) QXD_LT_GS(15)
+#undef QXD_LT_GS
+        }
+        k_lt_scale_dot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, W.lq[k], W.lp[k], W.lr, W.red.partials, W.lstate);
+        k_lt_update<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, W.lp[k], W.lq[k], W.lx, W.lr, W.red.partials, W.lstate);
+    }
+}
+
+// the cycle as a CUDA graph, captured once per work space (its pointers are fixed)
+int little_cycle_graph(qxd_lattice* lat, DflWork& W) {
+    if (W.cycle) return QXD_OK;
+    if (!W.cap) QXD_CUDA(cudaStreamCreateWithFlags(&W.cap, cudaStreamNonBlocking));
+    QXD_CUDA(cudaStreamBeginCapture(W.cap, cudaStreamCaptureModeThreadLocal));
+    little_cycle(lat, W, W.cap);
+    const cudaError_t le = cudaGetLastError();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(W.cap, &graph);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(le != cudaSuccess ? le : ce, "little solver graph capture");
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&W.cycle, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        W.cycle = nullptr;
+        return cuda_fail(ie, "cudaGraphInstantiate (little solver)");
+    }
     return QXD_OK;
 }
 
@@ -480,54 +737,22 @@ int little_gcr(qxd_lattice* lat, DflWork& W, double tol, int max_iter, int* iter
     *iters = 0;
     if (cc == 0.0) return QXD_OK;
     if (!std::isfinite(cc)) return fail(QXD_ERR_NUMERIC, "little solver: non-finite source");
-    const double target = tol * std::sqrt(cc);
     QXD_CUDA(cudaMemcpyAsync(W.lr, W.lc, bytes, cudaMemcpyDeviceToDevice, st));
-    double rn = std::sqrt(cc);
-    int it = 0;
-    while (it < max_iter && rn > target) {
-        int k = 0;
-        for (; k < DFL_NKV && it < max_iter && rn > target; ++k, ++it) {
-            QXD_CUDA(cudaMemcpyAsync(W.lp[k], W.lr, bytes, cudaMemcpyDeviceToDevice, st));
-            if ((rc = little_apply(lat, W, W.lq[k], W.lp[k], st))) return rc;
-            if (k > 0) {
-                VecList<double2> qs{};
-                VecList<double2> ps{};
-                for (int j = 0; j < k; ++j) {
-                    qs.p[j] = W.lq[j];
-                    ps.p[j] = W.lp[j];
-                }
-                cd a[BLAS_KMAX];
-                if ((rc = blas_mdot<double2>(W.red, n, k, qs, W.lq[k], a, st))) return rc;
-                CoefList cl{};
-                for (int j = 0; j < k; ++j) {
-                    cl.re[j] = a[j].real();
-                    cl.im[j] = a[j].imag();
-                }
-                double dummy;
-                if ((rc = blas_maxpy_norm<double2>(W.red, n, k, cl, qs, W.lq[k], &dummy, st))) return rc;
-                if ((rc = blas_maxpy_norm<double2>(W.red, n, k, cl, ps, W.lp[k], &dummy, st))) return rc;
-            }
-            double qq;
-            if ((rc = blas_norm2<double2>(W.red, n, W.lq[k], &qq, st))) return rc;
-            if (!(qq > 0.0) || !std::isfinite(qq)) return fail(QXD_ERR_NUMERIC, "little solver: breakdown");
-            const double s = 1.0 / std::sqrt(qq);
-            if ((rc = blas_scale<double2>(n, s, W.lq[k], st)) || (rc = blas_scale<double2>(n, s, W.lp[k], st)))
-                return rc;
-            VecList<double2> one{};
-            one.p[0] = W.lq[k];
-            cd al;
-            if ((rc = blas_mdot<double2>(W.red, n, 1, one, W.lr, &al, st))) return rc;
-            // x += al p_k ; r -= al q_k
-            if ((rc = blas_caxpy<double2>(n, -al, W.lp[k], W.lx, st))) return rc;
-            CoefList c1{};
-            c1.re[0] = al.real();
-            c1.im[0] = al.imag();
-            double r2;
-            if ((rc = blas_maxpy_norm<double2>(W.red, n, 1, c1, one, W.lr, &r2, st))) return rc;
-            rn = std::sqrt(r2);
-        }
+    LittleState& h = *W.h_lstate;
+    h = LittleState{};
+    h.rn2 = cc;
+    h.target2 = tol * tol * cc;
+    h.max_iter = max_iter;
+    h.done = (max_iter < 1 || tol >= 1.0) ? 1 : 0;
+    QXD_CUDA(cudaMemcpyAsync(W.lstate, &h, sizeof(LittleState), cudaMemcpyHostToDevice, st));
+    if ((rc = little_cycle_graph(lat, W))) return rc;
+    while (!h.done) {
+        QXD_CUDA(cudaGraphLaunch(W.cycle, st));
+        QXD_CUDA(cudaMemcpyAsync(&h, W.lstate, sizeof(LittleState), cudaMemcpyDeviceToHost, st));
+        QXD_CUDA(cudaStreamSynchronize(st));
     }
-    *iters = it;
+    if (h.status) return fail(QXD_ERR_NUMERIC, "little solver: breakdown or non-finite residual");
+    *iters = h.it;
     return QXD_OK;
 }
 

@@ -14,6 +14,18 @@ struct DflGeom {
     int nblk;
 };
 
+// device state of the little solver (one GCR step reads the coefficients
+// the previous kernels left here; the host reads it once per restart cycle)
+struct LittleState {
+    double a[2 * BLAS_KMAX];  // Gram-Schmidt coefficients <q_j, q_k>
+    double qq;                // |q_k|^2 after orthogonalisation
+    double al[2];             // <q_k, r> after normalisation
+    double rn2, target2;      // |r|^2, tol^2 |c|^2
+    int it, max_iter;         // steps taken, step limit
+    int done, status;         // status 1: breakdown or non-finite residual
+    unsigned count;           // blocks arrived at the current reduction
+};
+
 struct DflWork {
     int ns = 0;
     DflGeom d{};
@@ -26,6 +38,10 @@ struct DflWork {
     double2* lp[DFL_NKV] = {};
     double2* lq[DFL_NKV] = {};
     int* d_bad = nullptr;
+    LittleState* lstate = nullptr;    // device
+    LittleState* h_lstate = nullptr;  // pinned host copy
+    cudaStream_t cap = nullptr;       // capture stream of the cycle graph
+    cudaGraphExec_t cycle = nullptr;  // one restart cycle (DFL_NKV steps) of the little GCR
     Reducer red;
     SapWork sap;
     unsigned op_version = 0;   // operator the little operator was built for

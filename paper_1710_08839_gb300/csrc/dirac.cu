@@ -27,13 +27,16 @@ namespace qxd {
 
 namespace {
 
+// Both kernels apply D on the x0 planes [x0b, x0b + nx0) (all of them for
+// x0b = 0, nx0 = N0), nsites = nx0 N1 N2 N3 threads.
 // FP32: the pipelined hop order of hops_pipelined (128 registers)
 template <bool QNZ>
-__global__ void __launch_bounds__(DW_THREADS, DW_PP_MIN_BLOCKS) k_dirac32(Geom g, Fields<float> f, float q) {
+__global__ void __launch_bounds__(DW_THREADS, DW_PP_MIN_BLOCKS)
+    k_dirac32(Geom g, Fields<float> f, float q, int x0b, int nx0, int nsites) {
     const int tau = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tau >= g.V) return;
+    if (tau >= nsites) return;
     int x0, x1, x2, x3;
-    sweep_coords(g, tau, x0, x1, x2, x3);
+    sweep_coords_slab(g, x0b, nx0, tau, x0, x1, x2, x3);
     const int p = (x0 + x1 + x2 + x3) & 1;
     const int s = native_index(g, lex_index(g, x0, x1, x2, x3), p);
     int nb[8];
@@ -51,11 +54,12 @@ __global__ void __launch_bounds__(DW_THREADS, DW_PP_MIN_BLOCKS) k_dirac32(Geom g
 }
 
 template <typename R, bool QNZ>
-__global__ void __launch_bounds__(DW_THREADS, DwMinBlocks<R>::value) k_dirac(Geom g, Fields<R> f, R q) {
+__global__ void __launch_bounds__(DW_THREADS, DwMinBlocks<R>::value)
+    k_dirac(Geom g, Fields<R> f, R q, int x0b, int nx0, int nsites) {
     const int tau = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tau >= g.V) return;
+    if (tau >= nsites) return;
     int x0, x1, x2, x3;
-    sweep_coords(g, tau, x0, x1, x2, x3);
+    sweep_coords_slab(g, x0b, nx0, tau, x0, x1, x2, x3);
     const int p = (x0 + x1 + x2 + x3) & 1;
     const int s = native_index(g, lex_index(g, x0, x1, x2, x3), p);
     const int po = 1 - p;
@@ -109,25 +113,29 @@ __global__ void k_unpack(Geom g, const typename Fields<R>::vec* __restrict__ nat
 
 namespace {
 
-// D with launch shape sh (hop order, threads per block, sweep window)
-int launch_dirac_shape(qxd_lattice* lat, void* out, const void* in, int prec, const DwShape& sh, cudaStream_t st) {
+// D with launch shape sh (hop order, threads per block, sweep window) on the
+// x0 planes [x0b, x0b + nx0)
+int launch_dirac_shape(qxd_lattice* lat, void* out, const void* in, int prec, const DwShape& sh, cudaStream_t st,
+                       int x0b = 0, int nx0 = -1) {
     Geom g = lat->g;
     g.R = sh.rows;
-    const int blocks = (g.V + sh.threads - 1) / sh.threads;
+    if (nx0 < 0) nx0 = g.N0;
+    const int n = nx0 * g.N1 * g.N2 * g.N3;
+    const int blocks = (n + sh.threads - 1) / sh.threads;
     const bool qnz = lat->qhat != 0;
     if (prec == QXD_FP32) {
         Fields<float> f{(const float4*)in, (float4*)out, lat->U32, lat->A32, lat->C32};
         if (sh.pipelined) {
-            if (qnz) k_dirac32<true><<<blocks, sh.threads, 0, st>>>(g, f, (float)lat->qhat);
-            else k_dirac32<false><<<blocks, sh.threads, 0, st>>>(g, f, 0.f);
+            if (qnz) k_dirac32<true><<<blocks, sh.threads, 0, st>>>(g, f, (float)lat->qhat, x0b, nx0, n);
+            else k_dirac32<false><<<blocks, sh.threads, 0, st>>>(g, f, 0.f, x0b, nx0, n);
         } else {
-            if (qnz) k_dirac<float, true><<<blocks, sh.threads, 0, st>>>(g, f, (float)lat->qhat);
-            else k_dirac<float, false><<<blocks, sh.threads, 0, st>>>(g, f, 0.f);
+            if (qnz) k_dirac<float, true><<<blocks, sh.threads, 0, st>>>(g, f, (float)lat->qhat, x0b, nx0, n);
+            else k_dirac<float, false><<<blocks, sh.threads, 0, st>>>(g, f, 0.f, x0b, nx0, n);
         }
     } else {
         Fields<double> f{(const double2*)in, (double2*)out, lat->U64, lat->Zq64, lat->C64};
-        if (qnz) k_dirac<double, true><<<blocks, sh.threads, 0, st>>>(g, f, (double)lat->qhat);
-        else k_dirac<double, false><<<blocks, sh.threads, 0, st>>>(g, f, 0.0);
+        if (qnz) k_dirac<double, true><<<blocks, sh.threads, 0, st>>>(g, f, (double)lat->qhat, x0b, nx0, n);
+        else k_dirac<double, false><<<blocks, sh.threads, 0, st>>>(g, f, 0.0, x0b, nx0, n);
     }
     QXD_LAUNCHED("k_dirac");
     return QXD_OK;
@@ -203,6 +211,12 @@ int launch_dirac(qxd_lattice* lat, void* out, const void* in, int prec, cudaStre
         dw_shape_put(key, sh, autotune_enabled() ? "tuned" : "default");
     }
     return launch_dirac_shape(lat, out, in, prec, sh, st);
+}
+
+int launch_dirac_planes(qxd_lattice* lat, void* out, const void* in, int prec, int x0b, int nx0, cudaStream_t st) {
+    DwShape sh;
+    if (!dw_shape_get(dw_key(lat, prec), &sh)) sh = dw_default_shape(lat, prec);
+    return launch_dirac_shape(lat, out, in, prec, sh, st, x0b, nx0);
 }
 
 int launch_pack(qxd_lattice* lat, void* nat, const void* lex, int prec, cudaStream_t st) {

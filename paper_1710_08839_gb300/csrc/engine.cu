@@ -570,6 +570,25 @@ struct Engine {
 
 struct qxd_engine : public qxd::Engine {};
 
+namespace qxd {
+// checks of a request the engine accepts (also used by the server)
+int engine_check_request(qxd_lattice* op, void* x, const void* b, const qxd_solver_params* p, const char* who) {
+    const std::string w(who);
+    if (!op || !x || !b || !p) return fail(QXD_ERR_ARG, w + ": NULL argument");
+    const qxd_solver_params& P = *p;
+    if (!(P.tol > 0) || P.max_iter < 1 || P.nkv < 1 || P.nkv > BLAS_KMAX)
+        return fail(QXD_ERR_ARG, w + ": tol > 0, max_iter >= 1 and 1 <= nkv <= 16 required");
+    if (P.system != QXD_SOLVE_FULL || P.inner_prec != QXD_FP32 ||
+        (P.precond != QXD_PRECOND_SAP && P.precond != QXD_PRECOND_NONE) || (P.flags & ~0x100))
+        return fail(QXD_ERR_ARG, w + ": the engine runs full-system FGCR with FP32 inner vectors on device buffers");
+    if (P.precond == QXD_PRECOND_SAP && (P.sap_ncy < 1 || P.sap_nmr < 1))
+        return fail(QXD_ERR_ARG, w + ": sap_ncy and sap_nmr must be >= 1");
+    if (!clover_ready(op)) return fail(QXD_ERR_STATE, w + ": the operator needs qxd_sw_build");
+    if (P.precond == QXD_PRECOND_SAP) return sap_check(op);
+    return QXD_OK;
+}
+}  // namespace qxd
+
 using namespace qxd;
 
 extern "C" {
@@ -595,21 +614,10 @@ int qxd_engine_destroy(qxd_engine* e) {
 
 int qxd_engine_submit(qxd_engine* e, qxd_lattice* op, void* x, const void* b, const qxd_solver_params* p,
                       long long* id) {
-    if (!e || !op || !x || !b || !p || !id) return fail(QXD_ERR_ARG, "qxd_engine_submit: NULL argument");
+    if (!e || !id) return fail(QXD_ERR_ARG, "qxd_engine_submit: NULL argument");
+    int rc = engine_check_request(op, x, b, p, "qxd_engine_submit");
+    if (rc) return rc;
     const qxd_solver_params& P = *p;
-    if (!(P.tol > 0) || P.max_iter < 1 || P.nkv < 1 || P.nkv > BLAS_KMAX)
-        return fail(QXD_ERR_ARG, "qxd_engine_submit: tol > 0, max_iter >= 1 and 1 <= nkv <= 16 required");
-    if (P.system != QXD_SOLVE_FULL || P.inner_prec != QXD_FP32 ||
-        (P.precond != QXD_PRECOND_SAP && P.precond != QXD_PRECOND_NONE) || (P.flags & ~0x100))
-        return fail(QXD_ERR_ARG, "qxd_engine_submit: the engine runs full-system FGCR with FP32 inner vectors on "
-                                 "device buffers");
-    if (P.precond == QXD_PRECOND_SAP && (P.sap_ncy < 1 || P.sap_nmr < 1))
-        return fail(QXD_ERR_ARG, "qxd_engine_submit: sap_ncy and sap_nmr must be >= 1");
-    if (!clover_ready(op)) return fail(QXD_ERR_STATE, "qxd_engine_submit: the operator needs qxd_sw_build");
-    if (P.precond == QXD_PRECOND_SAP) {
-        int rc = sap_check(op);
-        if (rc) return rc;
-    }
     std::unique_ptr<Job> j(new (std::nothrow) Job());
     if (!j) return fail(QXD_ERR_OOM, "qxd_engine_submit: host allocation failed");
     j->id = e->next_id++;

@@ -79,6 +79,22 @@ __host__ __device__ __forceinline__ void sweep_coords(const Geom& g, int tau, in
     x2 = chunk * g.R + r;
 }
 
+// the same tiled order restricted to the x0 planes [x0b, x0b + nx0) (tau <
+// nx0 N1 N2 N3); with x0b = 0 and nx0 = N0 it is sweep_coords
+__host__ __device__ __forceinline__ void sweep_coords_slab(const Geom& g, int x0b, int nx0, int tau, int& x0, int& x1,
+                                                           int& x2, int& x3) {
+    const int rowlen = g.R * g.N3;
+    int within = tau % rowlen;
+    int rest = tau / rowlen;
+    x1 = rest % g.N1;
+    rest /= g.N1;
+    x0 = x0b + rest % nx0;
+    int chunk = rest / nx0;
+    int r = within / g.N3;
+    x3 = within - r * g.N3;
+    x2 = chunk * g.R + r;
+}
+
 // sweep over the sites of one parity p (tau < Vh), same tiled order
 __host__ __device__ __forceinline__ void sweep_coords_parity(const Geom& g, int p, int tau, int& x0, int& x1,
                                                              int& x2, int& x3) {
@@ -216,6 +232,7 @@ __host__ __device__ __forceinline__ cplx<R> times_mi(cplx<R> a) { return {a.im, 
 struct SolverWork;
 struct MscgWork;
 struct DflWork;
+struct HostPipe;
 }  // namespace qxd
 
 struct qxd_lattice {
@@ -251,6 +268,7 @@ struct qxd_lattice {
     void* scratch_out = nullptr;  // native spinor FP64-sized
     void* scratch_lex = nullptr;  // lexicographic FP64 spinor
     float4* sap_r = nullptr;      // FP32 residual of the Schwarz method (first FP32 SAP application)
+    qxd::HostPipe* hostpipe = nullptr;  // streams and events of the pipelined host-buffer D
 
     qxd::SolverWork* solver = nullptr;  // Krylov work vectors (first solve)
     qxd::MscgWork* mscg = nullptr;      // multi-shift CG work vectors (first use)
@@ -278,6 +296,16 @@ int launch_unpack(qxd_lattice* lat, void* lex, const void* nat, int prec, cudaSt
 bool host_device_view(const void* p, void** dev);
 int launch_pack_from_host(qxd_lattice* lat, void* nat, const void* lex_dev, int prec, cudaStream_t st);
 int launch_unpack_to_host(qxd_lattice* lat, void* lex_dev, const void* nat, int prec, cudaStream_t st);
+// out = D in on the x0 planes [x0b, x0b + nx0) only (native fields; the
+// launch shape of the full-lattice D)
+int launch_dirac_planes(qxd_lattice* lat, void* out, const void* in, int prec, int x0b, int nx0, cudaStream_t st);
+// out = D in for page-locked host buffers in the lexicographic layout,
+// pipelined over slabs of x0 planes (qxd_Dw's host path); QXD_ERR_ARG if the
+// lattice is too short in x0 to cut into slabs (then use the plain path)
+int dw_host_pipelined(qxd_lattice* lat, void* out_dev, const void* in_dev, int prec, cudaStream_t st);
+// slabs of the pipelined host path for x0 extent N0 (< 3: no pipeline)
+int pick_slabs(int N0);
+void release_hostio(qxd_lattice* lat);
 int ensure_scratch(qxd_lattice* lat);
 // the lattice that owns the gauge field (the lattice itself unless a view)
 inline qxd_lattice* gauge_owner(qxd_lattice* lat) { return lat->parent ? lat->parent : lat; }

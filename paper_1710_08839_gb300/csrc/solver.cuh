@@ -86,4 +86,7 @@ int sap_apply(qxd_lattice* lat, SapWork& w, void* out, const void* in, int ncy, 
 
 int run_solve(qxd_lattice* lat, const qxd_solver_params& P, qxd_solve_info& info, cudaStream_t st);
 
+// the checks qxd_engine_submit applies to a request (who: name in the message)
+int engine_check_request(qxd_lattice* op, void* x, const void* b, const qxd_solver_params* p, const char* who);
+
 }  // namespace qxd

@@ -119,6 +119,15 @@ SIGNATURES = {
     "qxd_engine_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
                               ctypes.POINTER(ctypes.c_longlong)]),
     "qxd_engine_graph_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+    "qxd_server_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(ctypes.c_longlong),
+                               ctypes.POINTER(ctypes.c_size_t), _i]),
+    "qxd_server_destroy": (_i, [_vp]),
+    "qxd_server_submit": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(qxd_solver_params),
+                               ctypes.POINTER(ctypes.c_longlong)]),
+    "qxd_server_poll": (_i, [_vp, ctypes.c_longlong, ctypes.POINTER(qxd_solve_info), ctypes.POINTER(_i)]),
+    "qxd_server_forget": (_i, [_vp, ctypes.c_longlong]),
+    "qxd_server_stats": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                              ctypes.POINTER(ctypes.c_longlong)]),
     "qxd_sw_logdet": (_i, [_vp, _i, ctypes.POINTER(_d)]),
     "qxd_mscg_defaults": (None, [ctypes.POINTER(qxd_mscg_params)]),
     "qxd_mscg": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_vp), _vp, ctypes.POINTER(qxd_mscg_params),
@@ -614,6 +623,69 @@ class Engine:
     def close(self):
         if self.handle:
             check(_call("qxd_engine_destroy", self.handle))
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving runtime (qxd_server_*): engine lanes by lattice size, each
+    with its own stream and worker thread. lane_sites: nlanes - 1 bounds on
+    the simulated sites; lane_budgets: bytes per lane."""
+
+    def __init__(self, lane_sites, lane_budgets, max_active=64):
+        n = len(lane_budgets)
+        if len(lane_sites) != n - 1:
+            raise ValueError("need len(lane_sites) == len(lane_budgets) - 1")
+        sites = (ctypes.c_longlong * max(1, n - 1))(*lane_sites)
+        budgets = (ctypes.c_size_t * n)(*[int(b) for b in lane_budgets])
+        h = _vp()
+        check(_call("qxd_server_create", ctypes.byref(h), n, sites, budgets, int(max_active)))
+        self.handle = h.value
+        self.nlanes = n
+        self._keep = {}
+        import threading
+        self._lock = threading.Lock()
+
+    def submit(self, op: "Lattice", x, b, **kw) -> int:
+        p = qxd_solver_defaults()
+        p.precond = QXD_PRECOND_SAP
+        p.inner_prec = QXD_FP32
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown solver parameter {k}")
+            setattr(p, k, v)
+        rid = ctypes.c_longlong()
+        check(_call("qxd_server_submit", self.handle, op.handle, x.data_ptr(), b.data_ptr(), ctypes.byref(p),
+                    ctypes.byref(rid)))
+        with self._lock:
+            self._keep[rid.value] = (op, x, b)
+        return rid.value
+
+    def poll(self, rid):
+        info = qxd_solve_info()
+        done = _i()
+        check(_call("qxd_server_poll", self.handle, ctypes.c_longlong(rid), ctypes.byref(info), ctypes.byref(done)))
+        return bool(done.value), info.as_dict()
+
+    def forget(self, rid):
+        check(_call("qxd_server_forget", self.handle, ctypes.c_longlong(rid)))
+        with self._lock:
+            self._keep.pop(rid, None)
+
+    def stats(self, lane):
+        a, c, s = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        check(_call("qxd_server_stats", self.handle, int(lane), ctypes.byref(a), ctypes.byref(c), ctypes.byref(s)))
+        return {"submitted": a.value, "completed": c.value, "steps": s.value}
+
+    def close(self):
+        if self.handle:
+            check(_call("qxd_server_destroy", self.handle))
             self.handle = None
             self._keep.clear()
 

@@ -70,11 +70,15 @@ def test_basis_and_little_operator_match_oracle(qxd, name):
     assert rel_max(got, Ao) < 2e-5
 
 
+@pytest.mark.parametrize("ns", [8, 16, 32, 6])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_deflated_solve(qxd, name):
+def test_deflated_solve(qxd, name, ns):
+    """Deflated SAP-GCR to 1e-10 through the oracle's D, with subspaces of
+    8, 16 and 32 fields (the warp-per-block little operator) and 6 (the
+    one-thread-per-row form)."""
     c = Case(**CASES[name])
     lat = c.lattice()
-    lat.dfl_subspace(8, niter=4, ncy=4, seed=7)
+    lat.dfl_subspace(ns, niter=4, ncy=4, seed=7)
     b = c.psi.to(torch.complex128).cuda().contiguous()
     x = torch.zeros_like(b)
     rc, info = lat.solve(x, b, tol=1e-10, precond=qxd.QXD_PRECOND_DFL_SAP, inner_prec=qxd.QXD_FP32)

@@ -106,6 +106,30 @@ def test_host_pointer_path_matches_device_path():
     lat.close()
 
 
+@pytest.mark.parametrize("T", [2, 6, 10, 14])
+def test_pipelined_host_path_matches_device_path(T):
+    """Page-locked input and output: qxd_Dw pipelines reading, applying and
+    writing over slabs of x0 planes (3, 5 and 7 slabs for T = 6, 10, 14; T = 2
+    cannot be cut and takes the unpipelined path). Same bits as the device
+    path, and the oracle's D."""
+    from paper_1710_08839_gb300 import qxd
+    c = Case(T=T, L1=4, L2=4, L3=2, qhat=2)
+    lat = c.lattice()
+    ref = c.oracle().apply(c.psi.numpy())
+    for prec, dt in ((qxd.QXD_FP64, torch.complex128), (qxd.QXD_FP32, torch.complex64)):
+        x = c.psi.to(dt).contiguous()
+        yd = torch.empty_like(x.cuda())
+        lat.Dw(yd, x.cuda())
+        xp, yp = x.pin_memory(), torch.full_like(x, float("nan")).pin_memory()
+        for _ in range(2):
+            lat.Dw(yp, xp)
+            torch.cuda.synchronize()
+            assert torch.equal(yp, yd.cpu())
+        got = yp.numpy().astype(np.complex128)
+        assert (rel_max(got, ref) < TOL64) if prec == qxd.QXD_FP64 else (rel_norm(got, ref) < TOL32)
+    lat.close()
+
+
 def test_native_layout_roundtrip_and_apply():
     from paper_1710_08839_gb300 import qxd
     c = Case(T=4, L1=4, L2=4, L3=4, qhat=2)
