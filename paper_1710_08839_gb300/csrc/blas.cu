@@ -1,11 +1,24 @@
 // Vector kernels of the Krylov solvers (see blas.cuh).
+//
+// FP32 vectors (float2) are combined in FP32 arithmetic; their inner
+// products and norms are summed in FP32 over runs of RUN products per
+// thread, and each run is added to an FP64 accumulator, which carries the
+// long sums over runs, threads and blocks. (GB300 does FP64 at 1/63 of the
+// FP32 rate: with every product in FP64, these kernels were bound by the
+// FP64 units instead of memory.) FP64 vectors use FP64 throughout.
 #include <new>
+#include <type_traits>
 
 #include "blas.cuh"
 
 namespace qxd {
 
 namespace {
+
+constexpr int RUN = 16;  // FP32 products summed before they join the FP64 accumulator
+
+template <typename T>
+constexpr bool is_f32() { return std::is_same<T, float2>::value; }
 
 __device__ __forceinline__ double2 ld(const float2* p, size_t i) {
     float2 v = p[i];
@@ -23,20 +36,86 @@ __global__ void k_reduce_final(const double* __restrict__ partials, int nc, doub
     res[c] = x;
 }
 
+// out[j] += conj(x_j[i]) y[i] for the elements i of this thread, FP32 runs
+// added to FP64 sums (the FP32 form of the multi-dot)
+__device__ __forceinline__ void mdot_f32(size_t n, int k, const float2* const* xs, const float2* __restrict__ y,
+                                         double acc[2 * BLAS_KMAX]) {
+    float run[2 * BLAS_KMAX];
+#pragma unroll
+    for (int c = 0; c < 2 * BLAS_KMAX; ++c) run[c] = 0.f;
+    int cnt = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 b = y[i];
+#pragma unroll
+        for (int j = 0; j < BLAS_KMAX; ++j) {
+            if (j >= k) break;
+            const float2 a = xs[j][i];
+            run[2 * j] = fmaf(a.x, b.x, fmaf(a.y, b.y, run[2 * j]));
+            run[2 * j + 1] = fmaf(a.x, b.y, fmaf(-a.y, b.x, run[2 * j + 1]));
+        }
+        if (++cnt == RUN) {
+#pragma unroll
+            for (int c = 0; c < 2 * BLAS_KMAX; ++c) {
+                acc[c] += run[c];
+                run[c] = 0.f;
+            }
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 2 * BLAS_KMAX; ++c) acc[c] += run[c];
+}
+
+// y -= sum_j c_j x_j in FP32 for the elements of this thread; acc[0] += |y|^2
+// (FP32 runs added to the FP64 sum)
+__device__ __forceinline__ void maxpy_norm_f32(size_t n, int k, const double* cre, const double* cim,
+                                               const float2* const* xs, float2* __restrict__ y, double* acc) {
+    float cr[BLAS_KMAX], ci[BLAS_KMAX];
+#pragma unroll
+    for (int j = 0; j < BLAS_KMAX; ++j) {
+        cr[j] = j < k ? (float)cre[j] : 0.f;
+        ci[j] = j < k ? (float)cim[j] : 0.f;
+    }
+    float run = 0.f;
+    int cnt = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float2 b = y[i];
+#pragma unroll
+        for (int j = 0; j < BLAS_KMAX; ++j) {
+            if (j >= k) break;
+            const float2 a = xs[j][i];
+            b.x = fmaf(-cr[j], a.x, fmaf(ci[j], a.y, b.x));
+            b.y = fmaf(-cr[j], a.y, fmaf(-ci[j], a.x, b.y));
+        }
+        y[i] = b;
+        run = fmaf(b.x, b.x, fmaf(b.y, b.y, run));
+        if (++cnt == RUN) {
+            acc[0] += run;
+            run = 0.f;
+            cnt = 0;
+        }
+    }
+    acc[0] += run;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_mdot(size_t n, int k, VecList<T> xs, const T* __restrict__ y,
                                                       double* __restrict__ partials) {
     double acc[2 * BLAS_KMAX];
 #pragma unroll
     for (int c = 0; c < 2 * BLAS_KMAX; ++c) acc[c] = 0.0;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const double2 b = ld(y, i);
+    if constexpr (is_f32<T>()) {
+        mdot_f32(n, k, xs.p, y, acc);
+    } else {
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+            const double2 b = ld(y, i);
 #pragma unroll
-        for (int j = 0; j < BLAS_KMAX; ++j) {
-            if (j >= k) break;
-            const double2 a = ld(xs.p[j], i);
-            acc[2 * j] += a.x * b.x + a.y * b.y;
-            acc[2 * j + 1] += a.x * b.y - a.y * b.x;
+            for (int j = 0; j < BLAS_KMAX; ++j) {
+                if (j >= k) break;
+                const double2 a = ld(xs.p[j], i);
+                acc[2 * j] += a.x * b.x + a.y * b.y;
+                acc[2 * j + 1] += a.x * b.y - a.y * b.x;
+            }
         }
     }
     block_reduce_store<2 * BLAS_KMAX>(acc, 2 * k, partials);
@@ -46,9 +125,24 @@ template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_norm2(size_t n, const T* __restrict__ x,
                                                        double* __restrict__ partials) {
     double acc[1] = {0.0};
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const double2 a = ld(x, i);
-        acc[0] += a.x * a.x + a.y * a.y;
+    if constexpr (is_f32<T>()) {
+        float run = 0.f;
+        int cnt = 0;
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+            const float2 a = x[i];
+            run = fmaf(a.x, a.x, fmaf(a.y, a.y, run));
+            if (++cnt == RUN) {
+                acc[0] += run;
+                run = 0.f;
+                cnt = 0;
+            }
+        }
+        acc[0] += run;
+    } else {
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+            const double2 a = ld(x, i);
+            acc[0] += a.x * a.x + a.y * a.y;
+        }
     }
     block_reduce_store<1>(acc, 1, partials);
 }
@@ -57,6 +151,11 @@ template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_maxpy_norm(size_t n, int k, CoefList c, VecList<T> xs,
                                                             T* __restrict__ y, double* __restrict__ partials) {
     double acc[1] = {0.0};
+    if constexpr (is_f32<T>()) {
+        maxpy_norm_f32(n, k, c.re, c.im, xs.p, y, acc);
+        block_reduce_store<1>(acc, 1, partials);
+        return;
+    }
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         double2 b = ld(y, i);
 #pragma unroll
@@ -75,6 +174,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_maxpy_norm(size_t n, int k, Coe
 
 template <typename T>
 __global__ void k_caxpy(size_t n, double cre, double cim, const T* __restrict__ x, T* __restrict__ y) {
+    if constexpr (is_f32<T>()) {
+        const float cr = (float)cre, ci = (float)cim;
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+            const float2 a = x[i];
+            float2 b = y[i];
+            b.x = fmaf(-cr, a.x, fmaf(ci, a.y, b.x));
+            b.y = fmaf(-cr, a.y, fmaf(-ci, a.x, b.y));
+            y[i] = b;
+        }
+        return;
+    }
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const double2 a = ld(x, i);
         double2 b = ld(y, i);
@@ -86,6 +196,14 @@ __global__ void k_caxpy(size_t n, double cre, double cim, const T* __restrict__ 
 
 template <typename T>
 __global__ void k_scale(size_t n, double s, T* __restrict__ x) {
+    if constexpr (is_f32<T>()) {
+        const float sf = (float)s;
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+            const float2 a = x[i];
+            x[i] = make_float2(a.x * sf, a.y * sf);
+        }
+        return;
+    }
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         double2 a = ld(x, i);
         a.x *= s;
@@ -100,20 +218,37 @@ __global__ void k_scale(size_t n, double s, T* __restrict__ x) {
 // number of sites of the array (V, or V/2 for a half-lattice field).
 __device__ __forceinline__ size_t f32_index(size_t S, size_t c, size_t s) { return (c >> 1) * 2 * S + 2 * s + (c & 1); }
 
-__global__ void k_update_x_native32(size_t S, int k, CoefList c, VecList<float2> vs, double2* __restrict__ x) {
-    for (size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (size_t)gridDim.x * blockDim.x) {
+// x64 += sum_j c_j v_j: the correction summed in FP32 (the v_j are FP32),
+// added to x in FP64
+__device__ __forceinline__ void update_x32_site(size_t S, size_t s, int k, const double* cre, const double* cim,
+                                                const float2* const* vs, double2* __restrict__ x) {
+    float cr[BLAS_KMAX], ci[BLAS_KMAX];
 #pragma unroll
-        for (int comp = 0; comp < 12; ++comp) {
-            double2 b = x[comp * S + s];
-            const size_t i32 = f32_index(S, comp, s);
-            for (int j = 0; j < k; ++j) {
-                const float2 a = vs.p[j][i32];
-                b.x += c.re[j] * a.x - c.im[j] * a.y;
-                b.y += c.re[j] * a.y + c.im[j] * a.x;
-            }
-            x[comp * S + s] = b;
-        }
+    for (int j = 0; j < BLAS_KMAX; ++j) {
+        cr[j] = j < k ? (float)cre[j] : 0.f;
+        ci[j] = j < k ? (float)cim[j] : 0.f;
     }
+#pragma unroll
+    for (int comp = 0; comp < 12; ++comp) {
+        const size_t i32 = f32_index(S, comp, s);
+        float dx = 0.f, dy = 0.f;
+#pragma unroll
+        for (int j = 0; j < BLAS_KMAX; ++j) {
+            if (j >= k) break;
+            const float2 a = vs[j][i32];
+            dx = fmaf(cr[j], a.x, fmaf(-ci[j], a.y, dx));
+            dy = fmaf(cr[j], a.y, fmaf(ci[j], a.x, dy));
+        }
+        double2 b = x[comp * S + s];
+        b.x += dx;
+        b.y += dy;
+        x[comp * S + s] = b;
+    }
+}
+
+__global__ void k_update_x_native32(size_t S, int k, CoefList c, VecList<float2> vs, double2* __restrict__ x) {
+    for (size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (size_t)gridDim.x * blockDim.x)
+        update_x32_site(S, s, k, c.re, c.im, vs.p, x);
 }
 
 __global__ void k_d2f_native(size_t S, const double2* __restrict__ in, float2* __restrict__ out) {
@@ -324,37 +459,15 @@ __global__ void __launch_bounds__(RED_THREADS) k_blas_batch(int op, const BJob* 
     const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t step = (size_t)gridDim.x * blockDim.x;
     if (op == B_MDOT_F32) {
+        // the same arithmetic as k_mdot<float2>, per job
         double acc[2 * BLAS_KMAX];
 #pragma unroll
         for (int c = 0; c < 2 * BLAS_KMAX; ++c) acc[c] = 0.0;
-        const float2* y = (const float2*)J.y;
-        for (size_t i = i0; i < J.n; i += step) {
-            const float2 bv = y[i];
-#pragma unroll
-            for (int j = 0; j < BLAS_KMAX; ++j) {
-                if (j >= J.k) break;
-                const float2 a = ((const float2*)J.xs[j])[i];
-                acc[2 * j] += (double)a.x * bv.x + (double)a.y * bv.y;
-                acc[2 * j + 1] += (double)a.x * bv.y - (double)a.y * bv.x;
-            }
-        }
+        mdot_f32(J.n, J.k, (const float2* const*)J.xs, (const float2*)J.y, acc);
         block_reduce_store_at(acc, 2 * J.k, part);
     } else if (op == B_MAXPY_NORM_F32) {
         double acc[1] = {0.0};
-        float2* y = (float2*)J.out;
-        for (size_t i = i0; i < J.n; i += step) {
-            double bx = y[i].x, by = y[i].y;
-#pragma unroll
-            for (int j = 0; j < BLAS_KMAX; ++j) {
-                if (j >= J.k) break;
-                const float2 a = ((const float2*)J.xs[j])[i];
-                bx -= J.cre[j] * a.x - J.cim[j] * a.y;
-                by -= J.cre[j] * a.y + J.cim[j] * a.x;
-            }
-            const float2 r = make_float2((float)bx, (float)by);
-            y[i] = r;
-            acc[0] += (double)r.x * r.x + (double)r.y * r.y;
-        }
+        maxpy_norm_f32(J.n, J.k, J.cre, J.cim, (const float2* const*)J.xs, (float2*)J.out, acc);
         block_reduce_store_at(acc, 1, part);
     } else if (op == B_NORM2_F64) {
         double acc[1] = {0.0};
@@ -374,9 +487,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_blas_batch(int op, const BJob* 
         block_reduce_store_at(acc, 1, part);
     } else if (op == B_SCALE_F32) {
         float2* x = (float2*)J.out;
+        const float sf = (float)J.s;
         for (size_t i = i0; i < J.n; i += step) {
             const float2 a = x[i];
-            x[i] = make_float2((float)(a.x * J.s), (float)(a.y * J.s));
+            x[i] = make_float2(a.x * sf, a.y * sf);
         }
     } else if (op == B_D2F_NATIVE) {
         const double2* in = (const double2*)J.y;
@@ -390,21 +504,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_blas_batch(int op, const BJob* 
             }
         }
     } else if (op == B_UPDATE_X_NATIVE32) {
-        double2* x = (double2*)J.out;
-        const size_t S = J.n;
-        for (size_t s = i0; s < S; s += step) {
-#pragma unroll
-            for (int comp = 0; comp < 12; ++comp) {
-                double2 bv = x[comp * S + s];
-                const size_t i32 = f32_index(S, comp, s);
-                for (int j = 0; j < J.k; ++j) {
-                    const float2 a = ((const float2*)J.xs[j])[i32];
-                    bv.x += J.cre[j] * a.x - J.cim[j] * a.y;
-                    bv.y += J.cre[j] * a.y + J.cim[j] * a.x;
-                }
-                x[comp * S + s] = bv;
-            }
-        }
+        for (size_t s = i0; s < J.n; s += step)
+            update_x32_site(J.n, s, J.k, J.cre, J.cim, (const float2* const*)J.xs, (double2*)J.out);
     }
 }
 

@@ -289,20 +289,36 @@ __global__ void __launch_bounds__(BSITES) k_dfl_project(Geom g, DflGeom d, int n
 // c[b][k] = <phi_{b,k}, eta>_b
 __global__ void __launch_bounds__(BSITES) k_dfl_restrict(Geom g, DflGeom d, int ns, const float4* __restrict__ basis,
                                                          const float4* __restrict__ eta, double2* __restrict__ c) {
-    __shared__ double sh[(BSITES / 32) * 2];
+    // c[b][k] = <phi_{b,k}, eta>_b: per site a 12-term dot in FP32, the block
+    // sums in FP64, eight k at a time (one block reduction per eight)
+    constexpr int KC = 8;
+    __shared__ double sh[(BSITES / 32) * 2 * KC];
     const int b = blockIdx.x;
     int x[4];
     block_site(g, d, b, threadIdx.x, x);
     const int s = native_at(g, x);
     cplx<float> e[12];
     load_spinor(eta, g.V, s, e);
-    for (int k = 0; k < ns; ++k) {
-        cplx<float> u[12];
-        load_spinor(basis + (size_t)k * 6 * g.V, g.V, s, u);
-        double v[2] = {0.0, 0.0};
-        cdot12(u, e, v[0], v[1]);
-        block_sum<2>(v, sh);
-        if (threadIdx.x == 0) c[(size_t)b * ns + k] = make_double2(v[0], v[1]);
+    for (int k0 = 0; k0 < ns; k0 += KC) {
+        double v[2 * KC];
+#pragma unroll
+        for (int kk = 0; kk < KC; ++kk) {
+            float re = 0.f, im = 0.f;
+            if (k0 + kk < ns) {
+                cplx<float> u[12];
+                load_spinor(basis + (size_t)(k0 + kk) * 6 * g.V, g.V, s, u);
+#pragma unroll
+                for (int i = 0; i < 12; ++i) {
+                    re = fmaf(u[i].re, e[i].re, fmaf(u[i].im, e[i].im, re));
+                    im = fmaf(u[i].re, e[i].im, fmaf(-u[i].im, e[i].re, im));
+                }
+            }
+            v[2 * kk] = re;
+            v[2 * kk + 1] = im;
+        }
+        block_sum<2 * KC>(v, sh);
+        if (threadIdx.x < KC && k0 + threadIdx.x < ns)
+            c[(size_t)b * ns + k0 + threadIdx.x] = make_double2(v[2 * threadIdx.x], v[2 * threadIdx.x + 1]);
     }
 }
 
