@@ -180,9 +180,13 @@ int qxd_eo_reconstruct(qxd_lattice* lat, void* x, const void* b, int flags, void
  * flags: precision and layout as for qxd_Dw, device buffers only. The
  * lattice needs every extent a multiple of 8 and, with C* boundaries,
  * L1 a multiple of 4 with L_k/4 + L1/4 even (else QXD_ERR_ARG). The first
- * FP32 application on a lattice (here or inside qxd_solve) allocates an FP32
- * residual field (96 bytes per site), kept with the lattice until
- * qxd_lattice_destroy.
+ * FP32 application on a lattice (here or inside qxd_solve) allocates two
+ * FP32 work fields (the last block corrections of every site and the block
+ * residuals of the even sites: 144 bytes per site), kept with the lattice
+ * until qxd_lattice_destroy. In FP32 the residual of a block visit is
+ * carried from the previous visits (the block solve's own residual plus the
+ * face-crossing hops of the other colour's corrections), which equals
+ * in - D out up to rounding.
  */
 int qxd_sap(qxd_lattice* lat, void* out, const void* in, int ncy, int nmr, int flags, void* stream);
 

@@ -12,15 +12,23 @@
 //         even-odd form D_hat_B = M_ee - H_eo M_oo^-1 H_oe of the block
 //   psi_B += delta
 // Starting from psi = 0, ncy cycles give psi = SAP(eta).
-// FP32, single lattice: k_sap_resid computes r = eta - D psi on the sites of
-// the colour in the L2-friendly sweep order of the D kernel (skipped while
-// psi = 0, where r = eta), then k_sap_split solves the blocks: two threads per
-// site pair, the block's interior compound links W' = -1/2 z^qhat U (all three
-// rows) and two block fields in shared memory, the clover blocks read through
-// L1. FP32, batched (k_sap_block_batch): the same block solve, each thread
-// computing its site's residual itself. FP64 (k_sap_block): one thread per
-// site pair, the block fields in shared memory, links and clover blocks from
-// the global fields.
+// FP32, single lattice (k_sap_split): two threads per site pair, the block's
+// interior compound links W' = -1/2 z^qhat U (all three rows) and two block
+// fields in shared memory, the clover blocks read through L1. The residual
+// of a block is not recomputed from eta - D psi: the even-odd block solve
+// leaves the block residual r_B - D_B delta equal to the MR residual rho on
+// the even sites and to zero on the odd sites (delta_o = M_oo^-1 (r_o - H_oe
+// delta_e) solves the odd rows exactly), and between two visits of a block
+// psi changes only on the blocks of the other colour, by their last
+// corrections delta. So a visit starts from
+//   r_B = rho_B (even sites), 0 (odd sites)  -  D_cross delta,
+// where D_cross keeps the hops of D that cross the faces of B (all other
+// terms of D delta vanish on B), and r_B = eta_B on the first visit. The
+// kernel keeps rho on the even sites and delta of every site in two work
+// fields. FP32, batched (k_sap_block_batch): the same block solve, each
+// thread computing its site's residual eta - D psi itself. FP64
+// (k_sap_block): one thread per site pair, the block fields in shared
+// memory, links and clover blocks from the global fields.
 #include <algorithm>
 #include <vector>
 
@@ -565,16 +573,70 @@ __device__ __forceinline__ void clover_half(const float4* __restrict__ C, int V,
     (void)sgn;
 }
 
+// Hop of D from x to its neighbour x + DIR mu across the face of x's block,
+// applied to the field d (raw: without the factor -1/2), added to acc
+template <bool QNZ, int MU, int DIR>
+__device__ __forceinline__ void crossing_hop(const Geom& g, const Fields<float>& f, const float4* __restrict__ d,
+                                             float q, const Site& t, int po, cplx<float> acc[12]) {
+    cplx<float> v[12], h0[3], h1[3], g0[3], g1[3], u[3][3];
+    const int sn = native_index(g, neighbour_lex<MU, DIR>(g, t.x[0], t.x[1], t.x[2], t.x[3]), po);
+    load_spinor(d, g.V, sn, v);
+    project<float, MU, DIR>(v, h0, h1);
+    const int sl = DIR > 0 ? t.s : sn;  // the link of x forwards, of the neighbour backwards
+    load_link(f.U, g.V, MU, sl, u);
+    if (DIR > 0) {
+        su3_mul(u, h0, g0);
+        su3_mul(u, h1, g1);
+    } else {
+        su3_dag_mul(u, h0, g0);
+        su3_dag_mul(u, h1, g1);
+    }
+    if (QNZ) {
+        const cplx<float> ph0 = link_phase(f.A, g.V, MU, sl, q);
+        const cplx<float> ph = DIR > 0 ? ph0 : conj(ph0);
+        times3(ph, g0);
+        times3(ph, g1);
+    }
+    accumulate<float, MU, DIR>(acc, g0, g1);
+}
+
+// acc += raw sum of the hops of D at site t that leave its block (t on the
+// upper face in mu: forward hop; on the lower face: backward hop)
+template <bool QNZ, int MU>
+__device__ __forceinline__ void crossing_dir(const Geom& g, const Fields<float>& f, const float4* __restrict__ d,
+                                             float q, const Site& t, int po, cplx<float> acc[12]) {
+    if (t.l[MU] == SAP_BS - 1) crossing_hop<QNZ, MU, +1>(g, f, d, q, t, po, acc);
+    if (t.l[MU] == 0) crossing_hop<QNZ, MU, -1>(g, f, d, q, t, po, acc);
+}
+
+// How k_sap_split forms the residual of its blocks and what it keeps
+enum SplitFlags : int {
+    SF_FIRST = 1,  // first visit of this colour: r = eta, psi = delta (psi is not read)
+    SF_CROSS = 2,  // subtract D_cross of the other colour's last corrections
+    SF_KEEP_RHO = 4,    // keep rho of the even sites for the next visit of this colour
+    SF_KEEP_DELTA = 8,  // keep delta for the next visit of the other colour
+};
+
+// Work fields of the single-lattice FP32 solve: delta of every site
+// (6 float4 per site, stride V) and rho of the even sites (stride Vh)
+struct SplitWork {
+    const float4* eta;
+    float4* delta;
+    float4* rho;
+    int flags;
+};
+
 // Same phases as sap_block_body, with the site-pair work split over the
-// two threads of a pair. The residual is computed one site per thread.
-// RIN: the residual r = eta - D psi of the blocks is read from rin (computed
-// by k_sap_resid over the whole colour, or eta itself while psi = 0);
-// otherwise every thread computes the residual of its site here.
-template <bool QNZ, bool RIN>
+// two threads of a pair.
+// BATCH: every thread computes the residual eta - D psi of its site (psi = 0
+// on the first launch, which also clears the other colour's blocks).
+// Otherwise the residual comes from the kept rho and the crossing hops of
+// the kept delta (SplitWork).
+template <bool QNZ, bool BATCH>
 __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm, int bidx, int colour, int psi_zero,
                                                const Fields<float>& f, const float4* __restrict__ Cinv,
-                                               const float4* __restrict__ eta, const float4* __restrict__ rin,
-                                               int nmr, float q) {
+                                               const float4* __restrict__ eta, const SplitWork& wk, int nmr,
+                                               float q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* sW4 = reinterpret_cast<float4*>(smem_raw);
     float2* sW2 = reinterpret_cast<float2*>(smem_raw + 16 * SPLIT_LINKS * sizeof(float4));
@@ -610,10 +672,10 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
     const Site so = make_site(g, org, base + 1 - par0);
     const Site& me = sg ? so : se;  // the site this thread stages, and whose residual it computes
 
-    // psi starts at zero. The first launch (colour 0) neither reads psi nor
-    // writes outside its blocks, so it also clears the partner block of the
-    // other colour, whose psi the next launch reads: no separate memset.
-    if (psi_zero) {
+    // psi starts at zero. The first batched launch (colour 0) neither reads
+    // psi nor writes outside its blocks, so it also clears the partner block
+    // of the other colour, whose psi the next launch reads: no separate memset.
+    if (BATCH && psi_zero) {
         const int o2[4] = {org[0], org[1], org[2], org3_other};
         const Site z = make_site(g, o2, me.lidx);
         float4* pz = const_cast<float4*>(f.psi);
@@ -647,8 +709,30 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
 
     {
         cplx<float> r[12];
-        if (RIN) load_spinor(rin, g.V, me.s, r);
-        else residual_body<float, QNZ>(g, f, eta, q, me, psi_zero, r);
+        if (BATCH) {
+            residual_body<float, QNZ>(g, f, eta, q, me, psi_zero, r);
+        } else {
+            if (wk.flags & SF_FIRST) {
+                load_spinor(wk.eta, g.V, me.s, r);
+            } else if (sg == 0) {  // even site: the kept rho
+                load_spinor(wk.rho, g.Vh, me.s, r);
+            } else {  // odd site: the block solve left no residual
+#pragma unroll
+                for (int i = 0; i < 12; ++i) r[i] = mk(0.f, 0.f);
+            }
+            if (wk.flags & SF_CROSS) {  // r -= D_cross delta = r + 1/2 (crossing hops of delta)
+                cplx<float> acc[12];
+#pragma unroll
+                for (int i = 0; i < 12; ++i) acc[i] = mk(0.f, 0.f);
+                const int po = 1 - sg;  // parity of the neighbours
+                crossing_dir<QNZ, 0>(g, f, wk.delta, q, me, po, acc);
+                crossing_dir<QNZ, 1>(g, f, wk.delta, q, me, po, acc);
+                crossing_dir<QNZ, 2>(g, f, wk.delta, q, me, po, acc);
+                crossing_dir<QNZ, 3>(g, f, wk.delta, q, me, po, acc);
+#pragma unroll
+                for (int i = 0; i < 12; ++i) r[i] = r[i] + 0.5f * acc[i];
+            }
+        }
         st_full(sg ? s_t : s_rho, t, r);
     }
     __syncthreads();
@@ -708,8 +792,22 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
                     rho[i] = rho[i] - om * w[i];
                 }
             }
-            if (step == nsteps - 2) st_half(s_t, sg, t, de);  // delta_e for the last step
-            else st_half(s_rho, sg, t, rho);
+            if (step == nsteps - 2) {
+                st_half(s_t, sg, t, de);  // delta_e for the last step
+                if (!BATCH && (wk.flags & SF_KEEP_RHO)) {
+                    // this thread's half of rho at the even site: components 3 sg + c and 6 + 3 sg + c
+                    float2* kr = reinterpret_cast<float2*>(wk.rho);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const int i = 6 * h + 3 * sg + c;
+                            kr[2 * ((size_t)(i >> 1) * g.Vh + se.s) + (i & 1)] = make_float2(rho[3 * h + c].re, rho[3 * h + c].im);
+                        }
+                }
+            } else {
+                st_half(s_rho, sg, t, rho);
+            }
         }
         __syncthreads();
     }
@@ -717,7 +815,8 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
     cplx<float> d[12];
     ld_full(sg ? s_rho : s_t, t, d);
     float4* psi = const_cast<float4*>(f.psi);
-    if (!psi_zero) {
+    if (!BATCH && (wk.flags & SF_KEEP_DELTA)) store_spinor(wk.delta, g.V, me.s, d);
+    if (BATCH ? !psi_zero : !(wk.flags & SF_FIRST)) {
         cplx<float> o[12];
         load_spinor(f.psi, g.V, me.s, o);
 #pragma unroll
@@ -729,11 +828,10 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
 template <bool QNZ>
 __global__ void __launch_bounds__(SPLIT_THREADS, 2) k_sap_split(const __grid_constant__ Geom g,
                                                                 const __grid_constant__ SapGeom sgm, int colour,
-                                                                int psi_zero, const __grid_constant__ Fields<float> f,
+                                                                const __grid_constant__ Fields<float> f,
                                                                 const float4* __restrict__ Cinv,
-                                                                const float4* __restrict__ eta,
-                                                                const float4* __restrict__ rin, int nmr, float q) {
-    sap_split_body<QNZ, true>(g, sgm, blockIdx.x, colour, psi_zero, f, Cinv, eta, rin, nmr, q);
+                                                                const __grid_constant__ SplitWork wk, int nmr, float q) {
+    sap_split_body<QNZ, false>(g, sgm, blockIdx.x, colour, 0, f, Cinv, nullptr, wk, nmr, q);
 }
 
 // batched form: thread block b works on block (b - cta_begin) of the job
@@ -748,49 +846,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 2) k_sap_block_batch(const SapJ
         else hi = mid - 1;
     }
     const SapJob& J = jobs[lo];
-    sap_split_body<true, false>(J.g, J.sg, b - J.cta_begin, colour, psi_zero, J.f, J.Cinv, J.eta, nullptr, nmr, J.q);
-}
-
-// r = eta - D psi at the sites of the blocks of colour `colour` (the residual
-// of a Schwarz half-cycle), one thread per site, written to r in the native
-// layout. The sites are visited in the tiled sweep order of the D kernel
-// restricted to the colour: in a row of x3 the colour changes every 4 sites,
-// so entry j of the row's N3/2 sites of the colour is
-// x3 = 8 (j / 4) + 4 k + j mod 4, k = (x0/4 + x1/4 + x2/4 + colour) mod 2.
-template <bool QNZ>
-__global__ void __launch_bounds__(DW_THREADS, DW_PP_MIN_BLOCKS)
-    k_sap_resid(const __grid_constant__ Geom g, int colour, const __grid_constant__ Fields<float> f,
-                const float4* __restrict__ eta, float4* __restrict__ r, float q) {
-    const int tau = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tau >= g.Vh) return;
-    const int half3 = g.N3 >> 1;
-    const int rowlen = g.R * half3;
-    const int within = tau % rowlen;
-    int rest = tau / rowlen;
-    const int x1 = rest % g.N1;
-    rest /= g.N1;
-    const int x0 = rest % g.N0;
-    const int chunk = rest / g.N0;
-    const int row = within / half3;
-    const int j = within - row * half3;
-    const int x2 = chunk * g.R + row;
-    const int k = ((x0 >> 2) + (x1 >> 2) + (x2 >> 2) + colour) & 1;
-    const int x3 = 8 * (j >> 2) + 4 * k + (j & 3);
-    const int p = (x0 + x1 + x2 + x3) & 1;
-    const int s = native_index(g, lex_index(g, x0, x1, x2, x3), p);
-    int nb[8];
-    neighbours8(g, x0, x1, x2, x3, 1 - p, nb);
-    cplx<float> acc[12];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) acc[i] = mk(0.f, 0.f);
-    hops_pipelined<QNZ>(f, g.V, s, nb, q, acc);
-    cplx<float> v[12], w[12];
-    load_spinor(f.psi, g.V, s, v);
-    clover_mul<true>(f.C, g.V, s, v, w);
-    load_spinor(eta, g.V, s, v);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) v[i] = v[i] - (w[i] - 0.5f * acc[i]);
-    store_spinor_cs(r, g.V, s, v);
+    sap_split_body<true, true>(J.g, J.sg, b - J.cta_begin, colour, psi_zero, J.f, J.Cinv, J.eta, SplitWork{}, nmr, J.q);
 }
 
 template <typename R>
@@ -817,27 +873,25 @@ int split_attrs(K kernel, size_t smem) {
     return QXD_OK;
 }
 
+// visit `cy` of colour `colour` out of ncy cycles
 template <typename R, bool QNZ>
-int launch_sap_block(qxd_lattice* lat, const SapGeom& sg, int colour, int psi_zero, Fields<R> f,
+int launch_sap_block(qxd_lattice* lat, const SapGeom& sg, int cy, int colour, int ncy, Fields<R> f,
                      const typename Fields<R>::cvec* Cinv, const typename Fields<R>::vec* eta, int nmr,
                      cudaStream_t st) {
     const size_t smem = sap_smem_bytes<R>();
     if constexpr (sizeof(R) == 4) {
-        // the residual of the colour: eta itself while psi = 0, else from k_sap_resid
-        const float4* rin = eta;
-        if (!psi_zero) {
-            const Geom& g = lat->g;
-            k_sap_resid<QNZ><<<(g.Vh + DW_THREADS - 1) / DW_THREADS, DW_THREADS, 0, st>>>(g, colour, f, eta, lat->sap_r,
-                                                                                      (float)lat->qhat);
-            QXD_LAUNCHED("k_sap_resid");
-            rin = lat->sap_r;
-        }
+        SplitWork wk{eta, lat->sap_r, lat->sap_r + (size_t)SPINOR_F4 * lat->g.V, 0};
+        if (cy == 0) wk.flags |= SF_FIRST;
+        if (cy > 0 || colour == 1) wk.flags |= SF_CROSS;  // the other colour has a correction
+        if (cy + 1 < ncy) wk.flags |= SF_KEEP_RHO;
+        if (cy + 1 < ncy || colour == 0) wk.flags |= SF_KEEP_DELTA;
         int rc = split_attrs(k_sap_split<QNZ>, smem);
         if (rc) return rc;
-        k_sap_split<QNZ><<<sg.nhalf, SPLIT_THREADS, smem, st>>>(lat->g, sg, colour, psi_zero, f, Cinv, eta, rin, nmr,
+        k_sap_split<QNZ><<<sg.nhalf, SPLIT_THREADS, smem, st>>>(lat->g, sg, colour, f, Cinv, wk, nmr,
                                                                 (float)lat->qhat);
         QXD_LAUNCHED("k_sap_split");
     } else {
+        const int psi_zero = (cy == 0 && colour == 0) ? 1 : 0;
         QXD_CUDA(cudaFuncSetAttribute(k_sap_block<R, QNZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_sap_block<R, QNZ><<<sg.nhalf, SAP_THREADS, smem, st>>>(lat->g, sg, colour, psi_zero, f, Cinv, eta, nmr,
                                                                   (R)lat->qhat);
@@ -893,23 +947,22 @@ int sap_apply(qxd_lattice* lat, SapWork& w, void* out, const void* in, int ncy, 
     const typename Fields<R>::cvec* Cinv = sap_cinv(lat, R(0));
     const typename Fields<R>::vec* eta = (const typename Fields<R>::vec*)in;
     const bool qnz = lat->qhat != 0;
-    // psi starts at zero: the first half-cycle writes the blocks of colour 0
-    // without reading psi, and the blocks of colour 1 must read zeros there
-    // (the FP32 kernel clears them itself in its first launch)
+    // FP64: psi starts at zero; the first half-cycle writes the blocks of
+    // colour 0 without reading psi, and the blocks of colour 1 must read zeros
+    // there. FP32: the first visit of each colour writes psi = delta.
     if (sizeof(R) == 8) QXD_CUDA(cudaMemsetAsync(out, 0, (size_t)g.V * 24 * sizeof(R), st));
-    if (sizeof(R) == 4 && !lat->sap_r) {
-        const cudaError_t e = cudaMalloc(&lat->sap_r, (size_t)g.V * SPINOR_F4 * sizeof(float4));
+    if (sizeof(R) == 4 && !lat->sap_r) {  // delta (V sites) and rho (Vh even sites)
+        const cudaError_t e = cudaMalloc(&lat->sap_r, ((size_t)g.V + g.Vh) * SPINOR_F4 * sizeof(float4));
         if (e != cudaSuccess) {
             lat->sap_r = nullptr;
-            return cuda_fail(e, "SAP: cudaMalloc(residual field)");
+            return cuda_fail(e, "SAP: cudaMalloc(work fields)");
         }
     }
     int rc;
     for (int cy = 0; cy < ncy; ++cy)
         for (int colour = 0; colour < 2; ++colour) {
-            const int psi_zero = (cy == 0 && colour == 0) ? 1 : 0;
-            rc = qnz ? launch_sap_block<R, true>(lat, sg, colour, psi_zero, f, Cinv, eta, nmr, st)
-                     : launch_sap_block<R, false>(lat, sg, colour, psi_zero, f, Cinv, eta, nmr, st);
+            rc = qnz ? launch_sap_block<R, true>(lat, sg, cy, colour, ncy, f, Cinv, eta, nmr, st)
+                     : launch_sap_block<R, false>(lat, sg, cy, colour, ncy, f, Cinv, eta, nmr, st);
             if (rc) return rc;
         }
     return QXD_OK;
