@@ -184,7 +184,8 @@ def write_traffic_record(csv_path):
     the kernel sources it was measured on."""
     import csv
     import statistics
-    hdr, per = None, {}
+    import re
+    hdr, per, kernel_names = None, {}, set()
     for r in csv.reader(open(csv_path)):
         if r and r[0] == "ID":
             hdr = r
@@ -193,13 +194,17 @@ def write_traffic_record(csv_path):
             d = dict(zip(hdr, r))
             if "k_dirac" in d["Kernel Name"]:
                 per.setdefault(d["ID"], {})[d["Metric Name"]] = float(d["Metric Value"])
+                m = re.search(r"(k_dirac\w*)<(\d+)>", d["Kernel Name"])
+                kernel_names.add(f"{m.group(1)}<{'true' if m.group(2) == '1' else 'false'}>" if m
+                                 else d["Kernel Name"][:60])
     tr = [v["dram__bytes_read.sum"] + v["dram__bytes_write.sum"] for v in per.values()]
     h = hashlib.sha256()
     for f in TRAFFIC_SOURCES:
         h.update(open(os.path.join(ROOT, f), "rb").read())
     w = WORKLOAD
     V = w["T"] * 2 * w["L1"] * w["L2"] * w["L3"]
-    rec = {"kernel": "k_dirac<float, qhat != 0> (FP32 D)", "workload": f"doubled {w['T']}x{2 * w['L1']}x"
+    names = sorted({n for n in kernel_names})
+    rec = {"kernel": ", ".join(names) + " (FP32 D, the launch shape chosen by the autotuner)", "workload": f"doubled {w['T']}x{2 * w['L1']}x"
            f"{w['L2']}x{w['L3']} C* lattice, {V} sites", "launches": len(tr),
            "bytes_per_launch": statistics.mean(tr),
            "read_bytes_per_launch": statistics.mean(v["dram__bytes_read.sum"] for v in per.values()),
@@ -208,7 +213,8 @@ def write_traffic_record(csv_path):
            "duration_ns_under_ncu": statistics.mean(v["gpu__time_duration.sum"] for v in per.values()),
            "command": "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum "
                       "--clock-control none -k regex:k_dirac -s 52 -c 5 --csv --log-file dirac_full_dram.csv "
-                      "python bench.py --steps 20 --warmup 3 --no-cpu-baseline --no-solve --no-variants --no-e2e",
+                      "python bench.py --steps 20 --warmup 3 --no-cpu-baseline --no-solve --no-batch --no-serve "
+                      "--no-variants --no-e2e (the first 49 launches are the autotuner's candidates)",
            "source_sha256": h.hexdigest(),
            "note": "full benchmark size, 1-pass metrics; stale once the kernel sources change"}
     out = os.path.join(ROOT, "profiles", "dirac_fp32_q2_traffic.json")

@@ -28,12 +28,12 @@ __device__ __forceinline__ double2 ld(const double2* p, size_t i) { return p[i];
 __device__ __forceinline__ void st_(float2* p, size_t i, double2 v) { p[i] = make_float2((float)v.x, (float)v.y); }
 __device__ __forceinline__ void st_(double2* p, size_t i, double2 v) { p[i] = v; }
 
-__global__ void k_reduce_final(const double* __restrict__ partials, int nc, double* __restrict__ res) {
-    const int c = threadIdx.x;
-    if (c >= nc) return;
-    double x = 0.0;
-    for (int b = 0; b < RED_BLOCKS; ++b) x += partials[(size_t)b * 2 * BLAS_KMAX + c];
-    res[c] = x;
+__global__ void __launch_bounds__(RED_FINAL_THREADS) k_reduce_final(const double* __restrict__ partials, int nc,
+                                                                     double* __restrict__ res) {
+    for (int c = threadIdx.x >> 5; c < nc; c += RED_FINAL_THREADS / 32) {
+        const double x = warp_sum_column(partials, c, RED_BLOCKS);
+        if ((threadIdx.x & 31) == 0) res[c] = x;
+    }
 }
 
 // out[j] += conj(x_j[i]) y[i] for the elements i of this thread, FP32 runs
@@ -305,7 +305,7 @@ inline int ew_blocks(size_t n) {
 }  // namespace
 
 int reduce_finish(Reducer& red, int nc, cudaStream_t st) {
-    k_reduce_final<<<1, 2 * BLAS_KMAX, 0, st>>>(red.partials, nc, red.d_res);
+    k_reduce_final<<<1, RED_FINAL_THREADS, 0, st>>>(red.partials, nc, red.d_res);
     QXD_LAUNCHED("k_reduce_final");
     QXD_CUDA(cudaMemcpyAsync(red.h_res, red.d_res, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
     QXD_CUDA(cudaStreamSynchronize(st));
@@ -509,13 +509,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_blas_batch(int op, const BJob* 
     }
 }
 
-__global__ void k_reduce_final_batch(const double* __restrict__ partials, int nc, double* __restrict__ res) {
-    const int c = threadIdx.x;
-    if (c >= nc) return;
+__global__ void __launch_bounds__(RED_FINAL_THREADS) k_reduce_final_batch(const double* __restrict__ partials,
+                                                                           int nc, double* __restrict__ res) {
     const double* p = partials + (size_t)blockIdx.x * RED_BLOCKS * 2 * BLAS_KMAX;
-    double x = 0.0;
-    for (int b = 0; b < RED_BLOCKS; ++b) x += p[(size_t)b * 2 * BLAS_KMAX + c];
-    res[(size_t)blockIdx.x * 2 * BLAS_KMAX + c] = x;
+    for (int c = threadIdx.x >> 5; c < nc; c += RED_FINAL_THREADS / 32) {
+        const double x = warp_sum_column(p, c, RED_BLOCKS);
+        if ((threadIdx.x & 31) == 0) res[(size_t)blockIdx.x * 2 * BLAS_KMAX + c] = x;
+    }
 }
 
 }  // namespace
@@ -562,7 +562,7 @@ int blas_batch(BatchReducer& red, BOp op, int jobs, int nc, cudaStream_t st) {
     k_blas_batch<<<grid, RED_THREADS, 0, st>>>((int)op, red.d_jobs, red.partials);
     QXD_LAUNCHED("k_blas_batch");
     if (!reduce) return QXD_OK;
-    k_reduce_final_batch<<<jobs, 2 * BLAS_KMAX, 0, st>>>(red.partials, nc, red.d_res);
+    k_reduce_final_batch<<<jobs, RED_FINAL_THREADS, 0, st>>>(red.partials, nc, red.d_res);
     QXD_LAUNCHED("k_reduce_final_batch");
     QXD_CUDA(cudaMemcpyAsync(red.h_res, red.d_res, sizeof(double) * (size_t)jobs * 2 * BLAS_KMAX,
                              cudaMemcpyDeviceToHost, st));

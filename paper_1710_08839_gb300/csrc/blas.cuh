@@ -1,8 +1,8 @@
 // Vector kernels of the Krylov solvers on flat complex arrays (FP32 as
 // float2, FP64 as double2). Inner products and norms accumulate in FP64 and
 // are reduced deterministically: a fixed grid writes per-block partial sums,
-// one block adds them in a fixed order, so the result does not depend on
-// timing or on other work on the GPU.
+// one block adds them in a fixed order (a warp per value), so the result does
+// not depend on timing or on other work on the GPU.
 #pragma once
 
 #include <complex>
@@ -55,6 +55,22 @@ __device__ __forceinline__ void block_reduce_store(const double v[NC], int nc, d
         partials[(size_t)blockIdx.x * 2 * BLAS_KMAX + threadIdx.x] = x;
     }
 }
+
+// Sum of column c of nblocks partial rows (stride 2 BLAS_KMAX) by one warp:
+// lane l adds rows l, l + 32, ... in order, then a butterfly of shuffles.
+// Every lane ends with the same bits (each level adds the same two values in
+// both lanes), and the order is fixed, so the sum is deterministic.
+__device__ __forceinline__ double warp_sum_column(const double* __restrict__ partials, int c, int nblocks) {
+    const int lane = threadIdx.x & 31;
+    double x = 0.0;
+    for (int b = lane; b < nblocks; b += 32) x += __ldcg(partials + (size_t)b * 2 * BLAS_KMAX + c);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// threads of the final reduction: one warp per column, columns taken in turn
+constexpr int RED_FINAL_THREADS = 256;
 
 // sums the RED_BLOCKS partials of the first nc values in a fixed order into
 // red.h_res[0..nc) (synchronises the stream)

@@ -104,6 +104,27 @@ __device__ __forceinline__ void block_sum(double v[NV], double* sh) {
     __syncthreads();
 }
 
+// Warp sum of 32 FP32 values per lane by recursive halving: at the level
+// with lane offset o each lane keeps one half of its values, adds the
+// partner's copy of that half and sends the other half, so that after five
+// levels (31 shuffles) lane l holds the sum over the warp of value l. The
+// tree is fixed, so the sum is deterministic.
+__device__ __forceinline__ float warp_reduce_scatter32(float v[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int lev = 0; lev < 5; ++lev) {
+        const int o = 16 >> lev, n = 16 >> lev;  // lane offset, values kept
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            const float send = hi ? v[i] : v[i + n];
+            const float keep = hi ? v[i + n] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
 // ---------------------------------------------------------------------------
 // random fields and block orthonormalisation
 // ---------------------------------------------------------------------------
@@ -286,21 +307,22 @@ __global__ void __launch_bounds__(BSITES) k_dfl_project(Geom g, DflGeom d, int n
 // restriction, prolongation, little operator
 // ---------------------------------------------------------------------------
 
-// c[b][k] = <phi_{b,k}, eta>_b
+// c[b][k] = <phi_{b,k}, eta>_b: per site a 12-term dot in FP32, sixteen k
+// at a time summed over each warp in FP32 (32 values by recursive halving)
+// and over the eight warps of the block in FP64
 __global__ void __launch_bounds__(BSITES) k_dfl_restrict(Geom g, DflGeom d, int ns, const float4* __restrict__ basis,
                                                          const float4* __restrict__ eta, double2* __restrict__ c) {
-    // c[b][k] = <phi_{b,k}, eta>_b: per site a 12-term dot in FP32, the block
-    // sums in FP64, eight k at a time (one block reduction per eight)
-    constexpr int KC = 8;
+    constexpr int KC = 16;
     __shared__ double sh[(BSITES / 32) * 2 * KC];
     const int b = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int x[4];
     block_site(g, d, b, threadIdx.x, x);
     const int s = native_at(g, x);
     cplx<float> e[12];
     load_spinor(eta, g.V, s, e);
     for (int k0 = 0; k0 < ns; k0 += KC) {
-        double v[2 * KC];
+        float v[2 * KC];
 #pragma unroll
         for (int kk = 0; kk < KC; ++kk) {
             float re = 0.f, im = 0.f;
@@ -316,9 +338,17 @@ __global__ void __launch_bounds__(BSITES) k_dfl_restrict(Geom g, DflGeom d, int 
             v[2 * kk] = re;
             v[2 * kk + 1] = im;
         }
-        block_sum<2 * KC>(v, sh);
+        sh[warp * 2 * KC + lane] = (double)warp_reduce_scatter32(v);  // value `lane` of this warp
+        __syncthreads();
+        if (threadIdx.x < 2 * KC) {
+            double y = 0.0;
+            for (int w = 0; w < BSITES / 32; ++w) y += sh[w * 2 * KC + threadIdx.x];
+            sh[threadIdx.x] = y;  // row 0 is read only by this thread and the write below
+        }
+        __syncthreads();
         if (threadIdx.x < KC && k0 + threadIdx.x < ns)
-            c[(size_t)b * ns + k0 + threadIdx.x] = make_double2(v[2 * threadIdx.x], v[2 * threadIdx.x + 1]);
+            c[(size_t)b * ns + k0 + threadIdx.x] = make_double2(sh[2 * threadIdx.x], sh[2 * threadIdx.x + 1]);
+        __syncthreads();
     }
 }
 
@@ -390,7 +420,8 @@ void DflWork::release() {
     basis = nullptr;
     A = nullptr;
     chi = tfield = H = nullptr;
-    lx = lr = lc = nullptr;
+    lx = lc = nullptr;
+    lr = nullptr;
     d_bad = nullptr;
     red.release();
     ns = 0;
@@ -414,15 +445,15 @@ int DflWork::ensure(const Geom& g, int ns_) {
         (rc = dalloc_bytes((void**)&tfield, 6 * V * sizeof(float4), "cudaMalloc(deflation field)")) ||
         (rc = dalloc_bytes((void**)&H, 4 * 6 * V * sizeof(float4), "cudaMalloc(deflation faces)")) ||
         (rc = dalloc_bytes((void**)&lx, nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
-        (rc = dalloc_bytes((void**)&lr, nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
+        (rc = dalloc_bytes((void**)&lr, nl * sizeof(float2), "cudaMalloc(little vectors)")) ||
         (rc = dalloc_bytes((void**)&lc, nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
         (rc = dalloc_bytes((void**)&d_bad, sizeof(int), "cudaMalloc(deflation status)")) ||
         (rc = dalloc_bytes((void**)&lstate, sizeof(LittleState), "cudaMalloc(little solver state)")))
         return rc;
     QXD_CUDA(cudaMallocHost(&h_lstate, sizeof(LittleState)));
     for (int k = 0; k < DFL_NKV; ++k)
-        if ((rc = dalloc_bytes((void**)&lp[k], nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
-            (rc = dalloc_bytes((void**)&lq[k], nl * sizeof(double2), "cudaMalloc(little vectors)")))
+        if ((rc = dalloc_bytes((void**)&lp[k], nl * sizeof(float2), "cudaMalloc(little vectors)")) ||
+            (rc = dalloc_bytes((void**)&lq[k], nl * sizeof(float2), "cudaMalloc(little vectors)")))
             return rc;
     if ((rc = red.init())) return rc;
     ns = ns_;
@@ -494,24 +525,55 @@ __device__ __forceinline__ bool last_block_finish(const double* __restrict__ par
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    if (threadIdx.x < nc) {
-        double x = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) x += __ldcg(partials + (size_t)b * 2 * BLAS_KMAX + threadIdx.x);
-        out[threadIdx.x] = x;
+    for (int c = threadIdx.x >> 5; c < nc; c += (int)(blockDim.x >> 5)) {
+        const double x = warp_sum_column(partials, c, (int)gridDim.x);
+        if ((threadIdx.x & 31) == 0) out[c] = x;
     }
     __syncthreads();
     if (threadIdx.x == 0) *count = 0u;
     return threadIdx.x == 0;
 }
 
+// Little solver. The Krylov vectors r, p_k, q_k are FP32 and their
+// arithmetic is FP32: the little system is solved only to a relative residual
+// of dfl_tol (1e-2 by default) as a preconditioner inside the flexible GCR,
+// and GB300's FP64 rate (1/63 of FP32, conversions included) made FP64
+// vectors the cost of a little step. The solution x and the source c stay
+// FP64; inner products are summed in FP32 within a thread and a warp and in
+// FP64 across warps and blocks, in a fixed order.
+
+// block-wide sum of NC FP32 values per thread (NC <= 32) into the FP64
+// partials of this block (RED_THREADS threads)
+template <int NC>
+__device__ __forceinline__ void block_reduce_store_f32(const float v[NC], double* __restrict__ partials) {
+    __shared__ double sh[RED_THREADS / 32][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if constexpr (NC <= 2) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            float x = v[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) sh[warp][c] = (double)x;
+        }
+    } else {
+        float w[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) w[c] = c < NC ? v[c] : 0.f;
+        sh[warp][lane] = (double)warp_reduce_scatter32(w);
+    }
+    __syncthreads();
+    if (threadIdx.x < NC) {
+        double y = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) y += sh[w][threadIdx.x];
+        partials[(size_t)blockIdx.x * 2 * BLAS_KMAX + threadIdx.x] = y;
+    }
+}
+
 // q = A r: q[b][k] = sum_j sum_l A[b][j][k][l] r[n_j(b)][l], one thread per
-// (b, k); also p = r. The little operator is stored in FP32 and the products
-// are taken and summed in FP32: the little system is solved only to a
-// relative residual of dfl_tol (1e-2 by default) as a preconditioner inside
-// the flexible GCR, and GB300's FP64 rate (1/63 of FP32) made the FP64 form
-// of this product the cost of a little step.
-__global__ void k_lt_apply(Geom g, DflGeom d, int ns, const float2* __restrict__ A, const double2* __restrict__ r,
-                           double2* __restrict__ p, double2* __restrict__ q, const LittleState* __restrict__ S) {
+// (b, k); also p = r (A and the products in FP32)
+__global__ void k_lt_apply(Geom g, DflGeom d, int ns, const float2* __restrict__ A, const float2* __restrict__ r,
+                           float2* __restrict__ p, float2* __restrict__ q, const LittleState* __restrict__ S) {
     if (S->done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= d.nblk * ns) return;
@@ -520,16 +582,14 @@ __global__ void k_lt_apply(Geom g, DflGeom d, int ns, const float2* __restrict__
     for (int j = 0; j < 9; ++j) {
         const int nb = j == 0 ? b : block_nbr(g, d, b, (j - 1) >> 1, (j & 1) ? +1 : -1);
         const float2* a = A + (((size_t)b * 9 + j) * ns + k) * ns;
-        const double2* v = r + (size_t)nb * ns;
+        const float2* v = r + (size_t)nb * ns;
         for (int l = 0; l < ns; ++l) {
-            const float2 al = a[l];
-            const double2 vd = v[l];
-            const float vx = (float)vd.x, vy = (float)vd.y;
-            re = fmaf(al.x, vx, fmaf(-al.y, vy, re));
-            im = fmaf(al.x, vy, fmaf(al.y, vx, im));
+            const float2 al = a[l], vl = v[l];
+            re = fmaf(al.x, vl.x, fmaf(-al.y, vl.y, re));
+            im = fmaf(al.x, vl.y, fmaf(al.y, vl.x, im));
         }
     }
-    q[i] = make_double2(re, im);
+    q[i] = make_float2(re, im);
     p[i] = r[i];
 }
 
@@ -537,28 +597,27 @@ __global__ void k_lt_apply(Geom g, DflGeom d, int ns, const float2* __restrict__
 // per block b; G = 32 / ns lanes share a row k, lane g of a row taking the
 // ns / G entries l in [g ns / G, (g + 1) ns / G), so that a warp reads
 // whole consecutive rows of A[b][j]; the G partial sums of a row are added
-// by warp shuffles
+// by warp shuffles. A is read once per step and streamed (evict-first), so
+// that the Krylov vectors stay in L2.
 template <int NS>
 __global__ void __launch_bounds__(32) k_lt_apply_warp(Geom g, DflGeom d, const float2* __restrict__ A,
-                                                      const double2* __restrict__ r, double2* __restrict__ p,
-                                                      double2* __restrict__ q, const LittleState* __restrict__ S) {
+                                                      const float2* __restrict__ r, float2* __restrict__ p,
+                                                      float2* __restrict__ q, const LittleState* __restrict__ S) {
     if (S->done) return;
     constexpr int G = 32 / NS, CH = NS / G;
     const int b = blockIdx.x, lane = threadIdx.x;
     const int k = lane / G, part = lane % G;
     float re = 0.f, im = 0.f;
-#pragma unroll 1
+#pragma unroll 3
     for (int j = 0; j < 9; ++j) {
         const int nb = j == 0 ? b : block_nbr(g, d, b, (j - 1) >> 1, (j & 1) ? +1 : -1);
         const float2* a = A + (((size_t)b * 9 + j) * NS + k) * NS + part * CH;
-        const double2* v = r + (size_t)nb * NS + part * CH;
+        const float2* v = r + (size_t)nb * NS + part * CH;
 #pragma unroll
         for (int l = 0; l < CH; ++l) {
-            const float2 al = a[l];
-            const double2 vd = v[l];
-            const float vx = (float)vd.x, vy = (float)vd.y;
-            re = fmaf(al.x, vx, fmaf(-al.y, vy, re));
-            im = fmaf(al.x, vy, fmaf(al.y, vx, im));
+            const float2 al = __ldcs(a + l), vl = v[l];
+            re = fmaf(al.x, vl.x, fmaf(-al.y, vl.y, re));
+            im = fmaf(al.x, vl.y, fmaf(al.y, vl.x, im));
         }
     }
 #pragma unroll
@@ -568,59 +627,58 @@ __global__ void __launch_bounds__(32) k_lt_apply_warp(Geom g, DflGeom d, const f
     }
     if (part == 0) {
         const size_t i = (size_t)b * NS + k;
-        q[i] = make_double2(re, im);
+        q[i] = make_float2(re, im);
         p[i] = r[i];
     }
 }
 
+// a_j = <q_j, q_k>, j < K
 template <int K>
-__global__ void __launch_bounds__(RED_THREADS) k_lt_mdot(size_t n, VecList<double2> qs,
-                                                         const double2* __restrict__ qk, double* partials,
-                                                         LittleState* S) {
-    if (S->done) return;
-    constexpr int k = K;
-    double v[2 * K];
-#pragma unroll
-    for (int c = 0; c < 2 * k; ++c) v[c] = 0.0;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const double2 y = qk[i];
-#pragma unroll
-        for (int j = 0; j < k; ++j) {
-            const double2 x = qs.p[j][i];
-            v[2 * j] += x.x * y.x + x.y * y.y;
-            v[2 * j + 1] += x.x * y.y - x.y * y.x;
-        }
-    }
-    block_reduce_store<2 * K>(v, 2 * k, partials);
-    last_block_finish(partials, 2 * k, S->a, &S->count);
-}
-
-template <int K>
-__global__ void __launch_bounds__(RED_THREADS) k_lt_orth(size_t n, VecList<double2> qs, VecList<double2> ps,
-                                                         double2* __restrict__ qk, double2* __restrict__ pk,
+__global__ void __launch_bounds__(RED_THREADS) k_lt_mdot(size_t n, VecList<float2> qs, const float2* __restrict__ qk,
                                                          double* partials, LittleState* S) {
     if (S->done) return;
-    constexpr int k = K;
-    double a[2 * K + 1];
+    float v[2 * K];
 #pragma unroll
-    for (int c = 0; c < 2 * k; ++c) a[c] = S->a[c];
-    double v[1] = {0.0};
+    for (int c = 0; c < 2 * K; ++c) v[c] = 0.f;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        double2 y = qk[i], z = pk[i];
+        const float2 y = qk[i];
 #pragma unroll
-        for (int j = 0; j < k; ++j) {
-            const double ar = a[2 * j], ai = a[2 * j + 1];
-            const double2 x = qs.p[j][i], w = ps.p[j][i];
+        for (int j = 0; j < K; ++j) {
+            const float2 x = qs.p[j][i];
+            v[2 * j] = fmaf(x.x, y.x, fmaf(x.y, y.y, v[2 * j]));
+            v[2 * j + 1] = fmaf(x.x, y.y, fmaf(-x.y, y.x, v[2 * j + 1]));
+        }
+    }
+    block_reduce_store_f32<2 * K>(v, partials);
+    last_block_finish(partials, 2 * K, S->a, &S->count);
+}
+
+// q_k -= sum_j a_j q_j, p_k -= sum_j a_j p_j; |q_k|^2
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS) k_lt_orth(size_t n, VecList<float2> qs, VecList<float2> ps,
+                                                         float2* __restrict__ qk, float2* __restrict__ pk,
+                                                         double* partials, LittleState* S) {
+    if (S->done) return;
+    float a[2 * K + 1];
+#pragma unroll
+    for (int c = 0; c < 2 * K; ++c) a[c] = (float)S->a[c];
+    float v[1] = {0.f};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float2 y = qk[i], z = pk[i];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const float ar = a[2 * j], ai = a[2 * j + 1];
+            const float2 x = qs.p[j][i], w = ps.p[j][i];
             y.x -= ar * x.x - ai * x.y;
             y.y -= ar * x.y + ai * x.x;
             z.x -= ar * w.x - ai * w.y;
             z.y -= ar * w.y + ai * w.x;
         }
         qk[i] = y;
-        if (k > 0) pk[i] = z;
-        v[0] += y.x * y.x + y.y * y.y;
+        if (K > 0) pk[i] = z;
+        v[0] = fmaf(y.x, y.x, fmaf(y.y, y.y, v[0]));
     }
-    block_reduce_store<1>(v, 1, partials);
+    block_reduce_store_f32<1>(v, partials);
     double qq;
     if (last_block_finish(partials, 1, &qq, &S->count)) {
         S->qq = qq;
@@ -631,46 +689,50 @@ __global__ void __launch_bounds__(RED_THREADS) k_lt_orth(size_t n, VecList<doubl
     }
 }
 
-__global__ void __launch_bounds__(RED_THREADS) k_lt_scale_dot(size_t n, double2* __restrict__ qk,
-                                                              double2* __restrict__ pk, const double2* __restrict__ r,
+// q_k, p_k /= |q_k|; al = <q_k, r>
+__global__ void __launch_bounds__(RED_THREADS) k_lt_scale_dot(size_t n, float2* __restrict__ qk,
+                                                              float2* __restrict__ pk, const float2* __restrict__ r,
                                                               double* partials, LittleState* S) {
     if (S->done) return;
-    const double sc = 1.0 / sqrt(S->qq);
-    double v[2] = {0.0, 0.0};
+    const float sc = (float)(1.0 / sqrt(S->qq));
+    float v[2] = {0.f, 0.f};
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        double2 x = qk[i], w = pk[i];
+        float2 x = qk[i], w = pk[i];
         x.x *= sc;
         x.y *= sc;
         w.x *= sc;
         w.y *= sc;
         qk[i] = x;
         pk[i] = w;
-        const double2 y = r[i];
-        v[0] += x.x * y.x + x.y * y.y;
-        v[1] += x.x * y.y - x.y * y.x;
+        const float2 y = r[i];
+        v[0] = fmaf(x.x, y.x, fmaf(x.y, y.y, v[0]));
+        v[1] = fmaf(x.x, y.y, fmaf(-x.y, y.x, v[1]));
     }
-    block_reduce_store<2>(v, 2, partials);
+    block_reduce_store_f32<2>(v, partials);
     last_block_finish(partials, 2, S->al, &S->count);
 }
 
-__global__ void __launch_bounds__(RED_THREADS) k_lt_update(size_t n, const double2* __restrict__ pk,
-                                                           const double2* __restrict__ qk, double2* __restrict__ x,
-                                                           double2* __restrict__ r, double* partials, LittleState* S) {
+// x += al p_k (FP64), r -= al q_k; |r|^2 and the stopping test
+__global__ void __launch_bounds__(RED_THREADS) k_lt_update(size_t n, const float2* __restrict__ pk,
+                                                           const float2* __restrict__ qk, double2* __restrict__ x,
+                                                           float2* __restrict__ r, double* partials, LittleState* S) {
     if (S->done) return;
     const double ar = S->al[0], ai = S->al[1];
-    double v[1] = {0.0};
+    const float fr = (float)ar, fi = (float)ai;
+    float v[1] = {0.f};
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const double2 p = pk[i], q = qk[i];
-        double2 xi = x[i], ri = r[i];
+        const float2 p = pk[i], q = qk[i];
+        double2 xi = x[i];
+        float2 ri = r[i];
         xi.x += ar * p.x - ai * p.y;
         xi.y += ar * p.y + ai * p.x;
-        ri.x -= ar * q.x - ai * q.y;
-        ri.y -= ar * q.y + ai * q.x;
+        ri.x -= fr * q.x - fi * q.y;
+        ri.y -= fr * q.y + fi * q.x;
         x[i] = xi;
         r[i] = ri;
-        v[0] += ri.x * ri.x + ri.y * ri.y;
+        v[0] = fmaf(ri.x, ri.x, fmaf(ri.y, ri.y, v[0]));
     }
-    block_reduce_store<1>(v, 1, partials);
+    block_reduce_store_f32<1>(v, partials);
     double rn2;
     if (last_block_finish(partials, 1, &rn2, &S->count)) {
         S->rn2 = rn2;
@@ -682,6 +744,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_lt_update(size_t n, const doubl
             S->done = 1;
         }
     }
+}
+
+// r = c (FP64 source to the FP32 residual)
+__global__ void k_lt_init(size_t n, const double2* __restrict__ c, float2* __restrict__ r) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        r[i] = make_float2((float)c[i].x, (float)c[i].y);
 }
 
 // the launches of one restart cycle (steps k = 0 .. DFL_NKV - 1)
@@ -697,7 +765,7 @@ void little_cycle(qxd_lattice* lat, DflWork& W, cudaStream_t st) {
         else
             k_lt_apply<<<(int)((n + 127) / 128), 128, 0, st>>>(lat->g, W.d, W.ns, W.A, W.lr, W.lp[k], W.lq[k],
                                                              W.lstate);
-        VecList<double2> qs{}, ps{};
+        VecList<float2> qs{}, ps{};
         for (int j = 0; j < k; ++j) {
             qs.p[j] = W.lq[j];
             ps.p[j] = W.lp[j];
@@ -753,7 +821,8 @@ int little_gcr(qxd_lattice* lat, DflWork& W, double tol, int max_iter, int* iter
     *iters = 0;
     if (cc == 0.0) return QXD_OK;
     if (!std::isfinite(cc)) return fail(QXD_ERR_NUMERIC, "little solver: non-finite source");
-    QXD_CUDA(cudaMemcpyAsync(W.lr, W.lc, bytes, cudaMemcpyDeviceToDevice, st));
+    k_lt_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, W.lc, W.lr);
+    QXD_LAUNCHED("k_lt_init");
     LittleState& h = *W.h_lstate;
     h = LittleState{};
     h.rn2 = cc;

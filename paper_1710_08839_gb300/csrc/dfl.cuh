@@ -34,9 +34,10 @@ struct DflWork {
     float4* chi = nullptr;     // prolongation (FP32 field)
     float4* tfield = nullptr;  // FP32 work field
     float4* H = nullptr;       // [4] face hops (FP32 fields)
-    double2 *lx = nullptr, *lr = nullptr, *lc = nullptr;  // little vectors [nblk * ns]
-    double2* lp[DFL_NKV] = {};
-    double2* lq[DFL_NKV] = {};
+    double2 *lx = nullptr, *lc = nullptr;  // little solution and source [nblk * ns] (FP64)
+    float2* lr = nullptr;                  // little residual (FP32)
+    float2* lp[DFL_NKV] = {};              // little Krylov vectors (FP32)
+    float2* lq[DFL_NKV] = {};
     int* d_bad = nullptr;
     LittleState* lstate = nullptr;    // device
     LittleState* h_lstate = nullptr;  // pinned host copy
