@@ -102,6 +102,8 @@ struct Job {
     // device vectors
     size_t f64_bytes = 0, f32_bytes = 0;
     void *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *t64 = nullptr, *rin = nullptr;
+    void* sapw = nullptr;  // work fields of the batched Schwarz solve (delta, rho of the even sites)
+    size_t sapw_bytes = 0;
     void* phi[BLAS_KMAX] = {};
     void* chi[BLAS_KMAX] = {};
     // solver state
@@ -116,12 +118,17 @@ struct Job {
     size_t charge = 0;  // job_bytes charged against the budget while admitted
 };
 
-// device bytes a request holds at most: four FP64 fields, the FP32 residual
-// and nkv Krylov pairs (allocated on demand, but charged at admission so that
+// FP32 work fields of a batched Schwarz solve: the last block corrections
+// of every site and the block residuals of the even sites
+size_t sap_work_bytes(const qxd_lattice* op) { return ((size_t)op->g.V + op->g.Vh) * 24 * sizeof(float); }
+
+// device bytes a request holds at most: four FP64 fields, the FP32 residual,
+// nkv Krylov pairs (allocated on demand, but charged at admission so that
 // the active requests stay within the budget whatever their Krylov depth)
+// and the Schwarz work fields (charged for every request)
 size_t job_bytes(const qxd_lattice* op, int nkv) {
     const size_t V = (size_t)op->g.V;
-    return V * 24 * sizeof(double) * 4 + V * 24 * sizeof(float) * (1 + 2 * (size_t)nkv);
+    return V * 24 * sizeof(double) * 4 + V * 24 * sizeof(float) * (1 + 2 * (size_t)nkv) + sap_work_bytes(op);
 }
 
 }  // namespace
@@ -158,6 +165,8 @@ struct Engine {
         pool.release(j->r64, j->f64_bytes);
         pool.release(j->t64, j->f64_bytes);
         pool.release(j->rin, j->f32_bytes);
+        pool.release(j->sapw, j->sapw_bytes);
+        j->sapw = nullptr;
         for (int i = 0; i < BLAS_KMAX; ++i) {
             pool.release(j->phi[i], j->f32_bytes);
             pool.release(j->chi[i], j->f32_bytes);
@@ -175,6 +184,11 @@ struct Engine {
         for (void** p : f64)
             if ((rc = pool.alloc(j->f64_bytes, p))) return rc;
         if ((rc = pool.alloc(j->f32_bytes, &j->rin))) return rc;
+        // the single-lattice Schwarz path keeps its work fields with the operator
+        if (j->P.precond == QXD_PRECOND_SAP && !big(j)) {
+            j->sapw_bytes = sap_work_bytes(j->op);
+            if ((rc = pool.alloc(j->sapw_bytes, &j->sapw))) return rc;
+        }
         // Krylov vectors are allocated when first used (SAP-preconditioned
         // GCR rarely needs all nkv of them)
         return QXD_OK;
@@ -323,6 +337,8 @@ struct Engine {
                 J.f = Fields<float>{(const float4*)j->phi[j->k], nullptr, j->op->U32, j->op->A32, j->op->C32};
                 J.Cinv = j->op->Cinv32;
                 J.eta = (const float4*)j->rin;
+                J.delta = (float4*)j->sapw;
+                J.rho = J.delta + (size_t)SPINOR_F4 * j->op->g.V;
                 J.q = (float)j->op->qhat;
                 sj.push_back(J);
             } else {

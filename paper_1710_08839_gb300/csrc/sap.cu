@@ -25,10 +25,10 @@
 // where D_cross keeps the hops of D that cross the faces of B (all other
 // terms of D delta vanish on B), and r_B = eta_B on the first visit. The
 // kernel keeps rho on the even sites and delta of every site in two work
-// fields. FP32, batched (k_sap_block_batch): the same block solve, each
-// thread computing its site's residual eta - D psi itself. FP64
-// (k_sap_block): one thread per site pair, the block fields in shared
-// memory, links and clover blocks from the global fields.
+// fields. FP32, batched (k_sap_block_batch): the same block solve over the
+// blocks of several lattices in one launch, each job with its own work
+// fields. FP64 (k_sap_block): one thread per site pair, the block fields in
+// shared memory, links and clover blocks from the global fields.
 #include <algorithm>
 #include <vector>
 
@@ -627,16 +627,13 @@ struct SplitWork {
 };
 
 // Same phases as sap_block_body, with the site-pair work split over the
-// two threads of a pair.
-// BATCH: every thread computes the residual eta - D psi of its site (psi = 0
-// on the first launch, which also clears the other colour's blocks).
-// Otherwise the residual comes from the kept rho and the crossing hops of
-// the kept delta (SplitWork).
-template <bool QNZ, bool BATCH>
-__device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm, int bidx, int colour, int psi_zero,
+// two threads of a pair; the residual comes from eta on the first visit of
+// a colour, else from the kept rho and the crossing hops of the kept delta
+// (SplitWork).
+template <bool QNZ>
+__device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm, int bidx, int colour,
                                                const Fields<float>& f, const float4* __restrict__ Cinv,
-                                               const float4* __restrict__ eta, const SplitWork& wk, int nmr,
-                                               float q) {
+                                               const SplitWork& wk, int nmr, float q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* sW4 = reinterpret_cast<float4*>(smem_raw);
     float2* sW2 = reinterpret_cast<float2*>(smem_raw + 16 * SPLIT_LINKS * sizeof(float4));
@@ -647,7 +644,7 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
     float* red = reinterpret_cast<float*>(sm + 24 * SAP_HALF);  // 3 * warps reduction slots
 
     // blocks (b0, b1, b2, b3e) and (.., b3e + 1), b3e even: one of each colour
-    int org[4], org3_other;
+    int org[4];
     {
         const int bi2 = 2 * bidx;
         const int b3e = bi2 % sgm.nb3;
@@ -661,7 +658,6 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
         org[1] = SAP_BS * b1;
         org[2] = SAP_BS * b2;
         org[3] = SAP_BS * b3;
-        org3_other = SAP_BS * (2 * b3e + 1 - b3);
     }
     const int t = threadIdx.x >> 1;
     const int sg = threadIdx.x & 1;
@@ -671,17 +667,6 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
     const Site se = make_site(g, org, base + par0);
     const Site so = make_site(g, org, base + 1 - par0);
     const Site& me = sg ? so : se;  // the site this thread stages, and whose residual it computes
-
-    // psi starts at zero. The first batched launch (colour 0) neither reads
-    // psi nor writes outside its blocks, so it also clears the partner block
-    // of the other colour, whose psi the next launch reads: no separate memset.
-    if (BATCH && psi_zero) {
-        const int o2[4] = {org[0], org[1], org[2], org3_other};
-        const Site z = make_site(g, o2, me.lidx);
-        float4* pz = const_cast<float4*>(f.psi);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) pz[(size_t)k * g.V + z.s] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
 
     // compound links W' = -1/2 z^qhat U of this thread's site that stay
     // inside the block (se has parity 0, so parity sg)
@@ -709,29 +694,25 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
 
     {
         cplx<float> r[12];
-        if (BATCH) {
-            residual_body<float, QNZ>(g, f, eta, q, me, psi_zero, r);
-        } else {
-            if (wk.flags & SF_FIRST) {
-                load_spinor(wk.eta, g.V, me.s, r);
-            } else if (sg == 0) {  // even site: the kept rho
-                load_spinor(wk.rho, g.Vh, me.s, r);
-            } else {  // odd site: the block solve left no residual
+        if (wk.flags & SF_FIRST) {
+            load_spinor(wk.eta, g.V, me.s, r);
+        } else if (sg == 0) {  // even site: the kept rho
+            load_spinor(wk.rho, g.Vh, me.s, r);
+        } else {  // odd site: the block solve left no residual
 #pragma unroll
-                for (int i = 0; i < 12; ++i) r[i] = mk(0.f, 0.f);
-            }
-            if (wk.flags & SF_CROSS) {  // r -= D_cross delta = r + 1/2 (crossing hops of delta)
-                cplx<float> acc[12];
+            for (int i = 0; i < 12; ++i) r[i] = mk(0.f, 0.f);
+        }
+        if (wk.flags & SF_CROSS) {  // r -= D_cross delta = r + 1/2 (crossing hops of delta)
+            cplx<float> acc[12];
 #pragma unroll
-                for (int i = 0; i < 12; ++i) acc[i] = mk(0.f, 0.f);
-                const int po = 1 - sg;  // parity of the neighbours
-                crossing_dir<QNZ, 0>(g, f, wk.delta, q, me, po, acc);
-                crossing_dir<QNZ, 1>(g, f, wk.delta, q, me, po, acc);
-                crossing_dir<QNZ, 2>(g, f, wk.delta, q, me, po, acc);
-                crossing_dir<QNZ, 3>(g, f, wk.delta, q, me, po, acc);
+            for (int i = 0; i < 12; ++i) acc[i] = mk(0.f, 0.f);
+            const int po = 1 - sg;  // parity of the neighbours
+            crossing_dir<QNZ, 0>(g, f, wk.delta, q, me, po, acc);
+            crossing_dir<QNZ, 1>(g, f, wk.delta, q, me, po, acc);
+            crossing_dir<QNZ, 2>(g, f, wk.delta, q, me, po, acc);
+            crossing_dir<QNZ, 3>(g, f, wk.delta, q, me, po, acc);
 #pragma unroll
-                for (int i = 0; i < 12; ++i) r[i] = r[i] + 0.5f * acc[i];
-            }
+            for (int i = 0; i < 12; ++i) r[i] = r[i] + 0.5f * acc[i];
         }
         st_full(sg ? s_t : s_rho, t, r);
     }
@@ -794,7 +775,7 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
             }
             if (step == nsteps - 2) {
                 st_half(s_t, sg, t, de);  // delta_e for the last step
-                if (!BATCH && (wk.flags & SF_KEEP_RHO)) {
+                if (wk.flags & SF_KEEP_RHO) {
                     // this thread's half of rho at the even site: components 3 sg + c and 6 + 3 sg + c
                     float2* kr = reinterpret_cast<float2*>(wk.rho);
 #pragma unroll
@@ -815,8 +796,8 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
     cplx<float> d[12];
     ld_full(sg ? s_rho : s_t, t, d);
     float4* psi = const_cast<float4*>(f.psi);
-    if (!BATCH && (wk.flags & SF_KEEP_DELTA)) store_spinor(wk.delta, g.V, me.s, d);
-    if (BATCH ? !psi_zero : !(wk.flags & SF_FIRST)) {
+    if (wk.flags & SF_KEEP_DELTA) store_spinor(wk.delta, g.V, me.s, d);
+    if (!(wk.flags & SF_FIRST)) {
         cplx<float> o[12];
         load_spinor(f.psi, g.V, me.s, o);
 #pragma unroll
@@ -831,13 +812,13 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 2) k_sap_split(const __grid_con
                                                                 const __grid_constant__ Fields<float> f,
                                                                 const float4* __restrict__ Cinv,
                                                                 const __grid_constant__ SplitWork wk, int nmr, float q) {
-    sap_split_body<QNZ, false>(g, sgm, blockIdx.x, colour, 0, f, Cinv, nullptr, wk, nmr, q);
+    sap_split_body<QNZ>(g, sgm, blockIdx.x, colour, f, Cinv, wk, nmr, q);
 }
 
 // batched form: thread block b works on block (b - cta_begin) of the job
 // whose range holds b (one launch serves every job of a batch)
 __global__ void __launch_bounds__(SPLIT_THREADS, 2) k_sap_block_batch(const SapJob* __restrict__ jobs, int njobs,
-                                                                      int colour, int psi_zero, int nmr) {
+                                                                      int colour, int flags, int nmr) {
     int lo = 0, hi = njobs - 1;
     const int b = blockIdx.x;
     while (lo < hi) {
@@ -846,7 +827,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 2) k_sap_block_batch(const SapJ
         else hi = mid - 1;
     }
     const SapJob& J = jobs[lo];
-    sap_split_body<true, true>(J.g, J.sg, b - J.cta_begin, colour, psi_zero, J.f, J.Cinv, J.eta, SplitWork{}, nmr, J.q);
+    const SplitWork wk{J.eta, J.delta, J.rho, flags};
+    sap_split_body<true>(J.g, J.sg, b - J.cta_begin, colour, J.f, J.Cinv, wk, nmr, J.q);
 }
 
 template <typename R>
@@ -873,6 +855,16 @@ int split_attrs(K kernel, size_t smem) {
     return QXD_OK;
 }
 
+// flags of visit `cy` of colour `colour` out of ncy cycles
+int split_flags(int cy, int colour, int ncy) {
+    int fl = 0;
+    if (cy == 0) fl |= SF_FIRST;
+    if (cy > 0 || colour == 1) fl |= SF_CROSS;  // the other colour has a correction
+    if (cy + 1 < ncy) fl |= SF_KEEP_RHO;
+    if (cy + 1 < ncy || colour == 0) fl |= SF_KEEP_DELTA;
+    return fl;
+}
+
 // visit `cy` of colour `colour` out of ncy cycles
 template <typename R, bool QNZ>
 int launch_sap_block(qxd_lattice* lat, const SapGeom& sg, int cy, int colour, int ncy, Fields<R> f,
@@ -880,11 +872,7 @@ int launch_sap_block(qxd_lattice* lat, const SapGeom& sg, int cy, int colour, in
                      cudaStream_t st) {
     const size_t smem = sap_smem_bytes<R>();
     if constexpr (sizeof(R) == 4) {
-        SplitWork wk{eta, lat->sap_r, lat->sap_r + (size_t)SPINOR_F4 * lat->g.V, 0};
-        if (cy == 0) wk.flags |= SF_FIRST;
-        if (cy > 0 || colour == 1) wk.flags |= SF_CROSS;  // the other colour has a correction
-        if (cy + 1 < ncy) wk.flags |= SF_KEEP_RHO;
-        if (cy + 1 < ncy || colour == 0) wk.flags |= SF_KEEP_DELTA;
+        const SplitWork wk{eta, lat->sap_r, lat->sap_r + (size_t)SPINOR_F4 * lat->g.V, split_flags(cy, colour, ncy)};
         int rc = split_attrs(k_sap_split<QNZ>, smem);
         if (rc) return rc;
         k_sap_split<QNZ><<<sg.nhalf, SPLIT_THREADS, smem, st>>>(lat->g, sg, colour, f, Cinv, wk, nmr,
@@ -996,10 +984,9 @@ namespace {
 
 void launch_batch_set(const SapJob* d_jobs, int njobs, int ctas, int ncy, int nmr, size_t smem, cudaStream_t st) {
     for (int cy = 0; cy < ncy; ++cy)
-        for (int colour = 0; colour < 2; ++colour) {
-            const int psi_zero = (cy == 0 && colour == 0) ? 1 : 0;
-            k_sap_block_batch<<<ctas, SPLIT_THREADS, smem, st>>>(d_jobs, njobs, colour, psi_zero, nmr);
-        }
+        for (int colour = 0; colour < 2; ++colour)
+            k_sap_block_batch<<<ctas, SPLIT_THREADS, smem, st>>>(d_jobs, njobs, colour, split_flags(cy, colour, ncy),
+                                                                 nmr);
 }
 
 // the executable graph of this launch set, captured on first use
@@ -1045,7 +1032,7 @@ int sap_apply_batch(std::vector<SapJob>& jobs, SapJob* d_jobs, int ncy, int nmr,
                     SapGraphCache* graphs) {
     if (jobs.empty()) return QXD_OK;
     int ctas = 0;
-    for (auto& J : jobs) {  // psi = 0 is set by the first launch itself
+    for (auto& J : jobs) {  // the first visit of each colour writes psi without reading it
         J.cta_begin = ctas;
         ctas += J.sg.nhalf;
     }

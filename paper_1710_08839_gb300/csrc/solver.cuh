@@ -29,6 +29,8 @@ struct SapJob {
     Fields<float> f;
     const float4* Cinv;
     const float4* eta;
+    float4* delta;  // work fields: last block corrections (V sites) and
+    float4* rho;    // block residuals of the even sites (Vh), 6 float4 each
     float q;
     int cta_begin;
 };
