@@ -7,16 +7,17 @@
 // with or allocated by CUDA); pageable buffers keep the copy path.
 //
 // qxd_Dw with page-locked buffers is pipelined over slabs of x0 planes: a
-// slab is a contiguous range of the lexicographic host buffer, and the D of
-// a slab needs the input of the slab and of its two neighbours in x0. Three
-// streams overlap copying slab k + 1 in (cudaMemcpyAsync, then the pack
-// kernel on the device), applying D to slab k, and unpacking and copying
-// slab k - 1 out: the copy engines use the link in both directions at once
-// while the SMs compute. (Kernels reading and writing the host buffers
+// slab is a contiguous range of the lexicographic host buffer. One stream
+// copies the input slabs in (cudaMemcpyAsync, then the pack kernel on the
+// device); as soon as slab k is in, D is applied to every output plane whose
+// x0 neighbours have arrived (up to the last plane but one of slab k), and
+// those planes are unpacked and copied out on a third stream. The two planes
+// that wrap around in x0 come last. The copy engines thus use the link in
+// both directions at once while the SMs compute, and the output stream
+// starts after one input slab. (Kernels reading and writing the host buffers
 // directly, in the same pipeline, were 8 % slower: they take SMs from D.)
 #include <cstdlib>
 #include <new>
-#include <vector>
 
 #include "dirac_common.cuh"
 
@@ -112,7 +113,7 @@ constexpr int kMaxSlabs = 16;
 struct HostPipe {
     cudaStream_t rd = nullptr, wr = nullptr;
     cudaEvent_t start = nullptr, done = nullptr;
-    cudaEvent_t in[kMaxSlabs] = {}, out[kMaxSlabs] = {};
+    cudaEvent_t in[kMaxSlabs] = {}, out[kMaxSlabs + 2] = {};
     void* stage_out = nullptr;  // device staging of the lexicographic output
     ~HostPipe() {
         if (stage_out) cudaFree(stage_out);
@@ -121,10 +122,10 @@ struct HostPipe {
         cudaEvent_t evs[] = {start, done};
         for (cudaEvent_t e : evs)
             if (e) cudaEventDestroy(e);
-        for (int k = 0; k < kMaxSlabs; ++k) {
-            if (in[k]) cudaEventDestroy(in[k]);
-            if (out[k]) cudaEventDestroy(out[k]);
-        }
+        for (cudaEvent_t e : in)
+            if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : out)
+            if (e) cudaEventDestroy(e);
     }
 };
 
@@ -137,18 +138,17 @@ int ensure_hostpipe(qxd_lattice* lat) {
     QXD_CUDA(cudaStreamCreateWithFlags(&h->wr, cudaStreamNonBlocking));
     QXD_CUDA(cudaEventCreateWithFlags(&h->start, cudaEventDisableTiming));
     QXD_CUDA(cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming));
-    for (int k = 0; k < kMaxSlabs; ++k) {
-        QXD_CUDA(cudaEventCreateWithFlags(&h->in[k], cudaEventDisableTiming));
-        QXD_CUDA(cudaEventCreateWithFlags(&h->out[k], cudaEventDisableTiming));
-    }
+    for (cudaEvent_t& e : h->in) QXD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (cudaEvent_t& e : h->out) QXD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return QXD_OK;
 }
 
-// slabs: the divisor of N0 nearest to 8 with at least 2 planes per slab
+// slabs: the largest divisor of N0 up to 16 with at least 2 planes per slab
+// (at least 3 slabs, else 0: no pipeline)
 int pick_slabs(int N0) {
     int best = 0;
     for (int S = 3; S <= kMaxSlabs; ++S)
-        if (N0 % S == 0 && N0 / S >= 2 && (best == 0 || std::abs(S - 8) < std::abs(best - 8))) best = S;
+        if (N0 % S == 0 && N0 / S >= 2) best = S;
     return best;
 }
 
@@ -180,21 +180,31 @@ int dw_host_pipelined(qxd_lattice* lat, void* out_dev, const void* in_dev, int p
             return rc;
         QXD_CUDA(cudaEventRecord(h.in[k], h.rd));
     }
-    // outputs 1 .. S-2 as their inputs arrive, then the two that wrap in x0
-    std::vector<int> order;
-    for (int k = 1; k + 1 < S; ++k) order.push_back(k);
-    order.push_back(S - 1);
-    order.push_back(0);
-    for (int k : order) {
-        QXD_CUDA(cudaStreamWaitEvent(st, h.in[(k + 1) % S], 0));
-        QXD_CUDA(cudaStreamWaitEvent(st, h.in[(k + S - 1) % S], 0));
-        if ((rc = launch_dirac_planes(lat, lat->scratch_out, lat->scratch_in, prec, k * planes, planes, st))) return rc;
-        QXD_CUDA(cudaEventRecord(h.out[k], st));
-        QXD_CUDA(cudaStreamWaitEvent(h.wr, h.out[k], 0));
-        if ((rc = unpack_to_host_sites(lat, h.stage_out, lat->scratch_out, prec, k * slab, slab, grid, h.wr))) return rc;
-        QXD_CUDA(cudaMemcpyAsync((char*)out_dev + k * slab * esz, (const char*)h.stage_out + k * slab * esz,
-                                 slab * esz, cudaMemcpyDefault, h.wr));
+    // output planes [lo, hi) once input slab k is in: up to the last plane but
+    // one of slab k (its forward neighbour is in slab k + 1); plane 0 (whose
+    // backward neighbour is plane N0 - 1) and plane N0 - 1 come last
+    const size_t plane = (size_t)g.N1 * g.N2 * g.N3;
+    auto out_range = [&](int lo, int hi, int ev) -> int {
+        if (hi <= lo) return QXD_OK;
+        int r = launch_dirac_planes(lat, lat->scratch_out, lat->scratch_in, prec, lo, hi - lo, st);
+        if (r) return r;
+        QXD_CUDA(cudaEventRecord(h.out[ev], st));
+        QXD_CUDA(cudaStreamWaitEvent(h.wr, h.out[ev], 0));
+        if ((r = unpack_to_host_sites(lat, h.stage_out, lat->scratch_out, prec, lo * plane, (hi - lo) * plane, grid,
+                                      h.wr)))
+            return r;
+        QXD_CUDA(cudaMemcpyAsync((char*)out_dev + lo * plane * esz, (const char*)h.stage_out + lo * plane * esz,
+                                 (hi - lo) * plane * esz, cudaMemcpyDefault, h.wr));
+        return QXD_OK;
+    };
+    for (int k = 0; k < S; ++k) {
+        QXD_CUDA(cudaStreamWaitEvent(st, h.in[k], 0));  // slabs 0 .. k are in (rd is in order)
+        const int lo = k == 0 ? 1 : k * planes - 1;
+        const int hi = k == S - 1 ? g.N0 - 1 : (k + 1) * planes - 1;
+        if ((rc = out_range(lo, hi, k))) return rc;
     }
+    if ((rc = out_range(g.N0 - 1, g.N0, S))) return rc;
+    if ((rc = out_range(0, 1, S + 1))) return rc;
     QXD_CUDA(cudaEventRecord(h.done, h.wr));
     QXD_CUDA(cudaStreamWaitEvent(st, h.done, 0));
     return QXD_OK;
