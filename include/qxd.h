@@ -351,7 +351,10 @@ int qxd_engine_graph_stats(const qxd_engine* e, long long* captures, long long* 
  * (qxd_engine_create with lane_budget[i] bytes and max_active) and its own
  * host worker thread, which admits, steps and retires that lane's requests
  * without waiting for the other lanes: a request on a small lattice does not
- * wait for the steps of large ones. A request's result is the engine's (the
+ * wait for the steps of large ones. The lanes' streams have graded CUDA
+ * priorities, the lane of the smallest lattices the highest, so that the GPU
+ * schedules a small request's thread blocks ahead of those still queued for
+ * large lattices. A request's result is the engine's (the
  * same, bit for bit, as the request solved alone). submit, poll, forget and
  * stats may be called from any thread. Buffers x and b and the operator must
  * stay valid and unchanged until the request is done. qxd_server_destroy

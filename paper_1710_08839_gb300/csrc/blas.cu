@@ -6,6 +6,7 @@
 // long sums over runs, threads and blocks. (GB300 does FP64 at 1/63 of the
 // FP32 rate: with every product in FP64, these kernels were bound by the
 // FP64 units instead of memory.) FP64 vectors use FP64 throughout.
+#include <algorithm>
 #include <new>
 #include <type_traits>
 
@@ -119,6 +120,124 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot(size_t n, int k, VecList<T
         }
     }
     block_reduce_store<2 * BLAS_KMAX>(acc, 2 * k, partials);
+}
+
+// Elements per loop iteration of the FP32 multi-vector kernels: with few
+// vectors a thread has too few loads in flight to cover the DRAM latency
+// (one dot product ran at 2.1 TB/s), so it takes U elements at a time.
+template <int K>
+constexpr int elems_per_iter() { return K <= 1 ? 4 : K <= 3 ? 2 : 1; }
+
+// FP32 multi-dot over K <= 8 vectors with the vector count fixed at compile
+// time (K sums in FP32 runs and FP64 registers, K pointers): the general form
+// with 16 of each spills and reads at 0.4 of the HBM bandwidth. Partials go to
+// columns [col0, col0 + 2K) of each block's row.
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS) k_mdot32(size_t n, VecList<float2> xs, const float2* __restrict__ y,
+                                                        double* __restrict__ partials, int col0) {
+    constexpr int U = elems_per_iter<K>();
+    float run[2 * K];
+    double acc[2 * K];
+#pragma unroll
+    for (int c = 0; c < 2 * K; ++c) {
+        run[c] = 0.f;
+        acc[c] = 0.0;
+    }
+    int cnt = 0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
+        float2 b[U], a[U][K];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t i = i0 + u * stride;
+            b[u] = i < n ? y[i] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < K; ++j) a[u][j] = i < n ? xs.p[j][i] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                run[2 * j] = fmaf(a[u][j].x, b[u].x, fmaf(a[u][j].y, b[u].y, run[2 * j]));
+                run[2 * j + 1] = fmaf(a[u][j].x, b[u].y, fmaf(-a[u][j].y, b[u].x, run[2 * j + 1]));
+            }
+        if ((cnt += U) >= RUN) {
+#pragma unroll
+            for (int c = 0; c < 2 * K; ++c) {
+                acc[c] += run[c];
+                run[c] = 0.f;
+            }
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 2 * K; ++c) acc[c] += run[c];
+    block_reduce_store<2 * K>(acc, 2 * K, partials + col0);
+}
+
+// y -= sum_j c_j x_j in FP32 over K <= 16 vectors (count fixed at compile
+// time); |y|^2 of the result in FP32 runs added to an FP64 sum
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS) k_maxpy_norm32(size_t n, CoefList c, VecList<float2> xs,
+                                                              float2* __restrict__ y, double* __restrict__ partials) {
+    constexpr int U = elems_per_iter<K>();
+    float cr[K], ci[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        cr[j] = (float)c.re[j];
+        ci[j] = (float)c.im[j];
+    }
+    float run = 0.f;
+    double acc[1] = {0.0};
+    int cnt = 0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
+        float2 b[U], a[U][K];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t i = i0 + u * stride;
+            b[u] = i < n ? y[i] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < K; ++j) a[u][j] = i < n ? xs.p[j][i] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t i = i0 + u * stride;
+            if (i >= n) continue;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                b[u].x = fmaf(-cr[j], a[u][j].x, fmaf(ci[j], a[u][j].y, b[u].x));
+                b[u].y = fmaf(-cr[j], a[u][j].y, fmaf(-ci[j], a[u][j].x, b[u].y));
+            }
+            y[i] = b[u];
+            run = fmaf(b[u].x, b[u].x, fmaf(b[u].y, b[u].y, run));
+        }
+        if ((cnt += U) >= RUN) {
+            acc[0] += run;
+            run = 0.f;
+            cnt = 0;
+        }
+    }
+    acc[0] += run;
+    block_reduce_store<1>(acc, 1, partials);
+}
+
+// vectors [j0, j0 + kk) of xs, kk <= 8
+int launch_mdot32(size_t n, int j0, int kk, const VecList<float2>& xs, const float2* y, double* partials,
+                  cudaStream_t st) {
+    VecList<float2> sub{};
+    for (int j = 0; j < kk; ++j) sub.p[j] = xs.p[j0 + j];
+    const int col0 = 2 * j0;
+    switch (kk) {
+#define QXD_MDOT32(K) \
+    case K: k_mdot32<K><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, sub, y, partials, col0); break;
+        QXD_MDOT32(1) QXD_MDOT32(2) QXD_MDOT32(3) QXD_MDOT32(4) QXD_MDOT32(5) QXD_MDOT32(6) QXD_MDOT32(7)
+        QXD_MDOT32(8)
+#undef QXD_MDOT32
+        default: return fail(QXD_ERR_ARG, "multi-dot: bad vector count");
+    }
+    QXD_LAUNCHED("k_mdot32");
+    return QXD_OK;
 }
 
 template <typename T>
@@ -330,8 +449,16 @@ void Reducer::release() {
 template <typename T>
 int blas_mdot(Reducer& red, size_t n, int k, const VecList<T>& xs, const T* y, cd* out, cudaStream_t st) {
     if (k <= 0) return QXD_OK;
-    k_mdot<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, xs, y, red.partials);
-    QXD_LAUNCHED("k_mdot");
+    if constexpr (is_f32<T>()) {
+        // at most 8 vectors per pass (y read once per pass)
+        for (int j0 = 0; j0 < k; j0 += 8) {
+            const int rc = launch_mdot32(n, j0, std::min(8, k - j0), xs, y, red.partials, st);
+            if (rc) return rc;
+        }
+    } else {
+        k_mdot<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, xs, y, red.partials);
+        QXD_LAUNCHED("k_mdot");
+    }
     int rc = reduce_finish(red, 2 * k, st);
     if (rc) return rc;
     for (int j = 0; j < k; ++j) out[j] = cd(red.h_res[2 * j], red.h_res[2 * j + 1]);
@@ -351,8 +478,22 @@ int blas_norm2(Reducer& red, size_t n, const T* x, double* out, cudaStream_t st)
 template <typename T>
 int blas_maxpy_norm(Reducer& red, size_t n, int k, const CoefList& c, const VecList<T>& xs, T* y, double* nrm2,
                     cudaStream_t st) {
-    k_maxpy_norm<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, c, xs, y, red.partials);
-    QXD_LAUNCHED("k_maxpy_norm");
+    if constexpr (is_f32<T>()) {
+        switch (k) {
+#define QXD_MAXPY32(K) \
+    case K: k_maxpy_norm32<K><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, c, xs, y, red.partials); break;
+            QXD_MAXPY32(1) QXD_MAXPY32(2) QXD_MAXPY32(3) QXD_MAXPY32(4) QXD_MAXPY32(5) QXD_MAXPY32(6)
+            QXD_MAXPY32(7) QXD_MAXPY32(8) QXD_MAXPY32(9) QXD_MAXPY32(10) QXD_MAXPY32(11) QXD_MAXPY32(12)
+            QXD_MAXPY32(13) QXD_MAXPY32(14) QXD_MAXPY32(15) QXD_MAXPY32(16)
+#undef QXD_MAXPY32
+            case 0: k_norm2<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, y, red.partials); break;  // nothing to subtract
+            default: return fail(QXD_ERR_ARG, "multi-axpy: bad vector count");
+        }
+        QXD_LAUNCHED("k_maxpy_norm32");
+    } else {
+        k_maxpy_norm<T><<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, k, c, xs, y, red.partials);
+        QXD_LAUNCHED("k_maxpy_norm");
+    }
     int rc = reduce_finish(red, 1, st);
     if (rc) return rc;
     *nrm2 = red.h_res[0];

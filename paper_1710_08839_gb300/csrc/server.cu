@@ -6,6 +6,7 @@
 // of the largest). Requests are submitted and polled from any thread; the
 // worker of a lane is the only thread that touches its engine. The paper
 // solves one system at a time; this is a serving design of this library.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -149,6 +150,12 @@ int qxd_server_create(qxd_server** out, int nlanes, const long long* lane_sites,
     if (!s) return fail(QXD_ERR_OOM, "qxd_server_create: host allocation failed");
     cudaError_t e = cudaGetDevice(&s->device);
     if (e != cudaSuccess) return cuda_fail(e, "qxd_server_create: cudaGetDevice");
+    // stream priorities: the lane of the smallest lattices on the highest, so
+    // that the thread blocks of short requests are scheduled as soon as blocks
+    // of the large lattices' kernels retire, instead of after those kernels
+    int least = 0, greatest = 0;
+    if ((e = cudaDeviceGetStreamPriorityRange(&least, &greatest)) != cudaSuccess)
+        return cuda_fail(e, "qxd_server_create: cudaDeviceGetStreamPriorityRange");
     for (int i = 0; i < nlanes; ++i) {
         std::unique_ptr<Lane> L(new (std::nothrow) Lane());
         if (!L) {
@@ -157,7 +164,8 @@ int qxd_server_create(qxd_server** out, int nlanes, const long long* lane_sites,
         }
         L->max_sites = i + 1 < nlanes ? lane_sites[i] : -1;
         L->budget = lane_budget[i];
-        if ((e = cudaStreamCreateWithFlags(&L->st, cudaStreamNonBlocking)) != cudaSuccess) {
+        const int prio = std::max(greatest, least - (nlanes - 1 - i));  // greatest is numerically lowest
+        if ((e = cudaStreamCreateWithPriority(&L->st, cudaStreamNonBlocking, prio)) != cudaSuccess) {
             s->shutdown();
             return cuda_fail(e, "qxd_server_create: cudaStreamCreate");
         }
