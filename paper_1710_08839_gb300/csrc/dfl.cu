@@ -408,7 +408,7 @@ void DflWork::release() {
     cycle = nullptr;
     cap = nullptr;
     h_lstate = nullptr;
-    void* ps[] = {basis, A, chi, tfield, H, lx, lr, lc, d_bad, lstate};
+    void* ps[] = {basis, A, chi, tfield, H, lx, lr, lc, lt, Ainv, d_bad, lstate};
     for (void* p : ps)
         if (p) cudaFree(p);
     lstate = nullptr;
@@ -421,7 +421,8 @@ void DflWork::release() {
     A = nullptr;
     chi = tfield = H = nullptr;
     lx = lc = nullptr;
-    lr = nullptr;
+    lr = lt = Ainv = nullptr;
+    eo = false;
     d_bad = nullptr;
     red.release();
     ns = 0;
@@ -446,6 +447,9 @@ int DflWork::ensure(const Geom& g, int ns_) {
         (rc = dalloc_bytes((void**)&H, 4 * 6 * V * sizeof(float4), "cudaMalloc(deflation faces)")) ||
         (rc = dalloc_bytes((void**)&lx, nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
         (rc = dalloc_bytes((void**)&lr, nl * sizeof(float2), "cudaMalloc(little vectors)")) ||
+        (rc = dalloc_bytes((void**)&lt, nl * sizeof(float2), "cudaMalloc(little vectors)")) ||
+        (rc = dalloc_bytes((void**)&Ainv, (size_t)d.nblk * ns_ * ns_ * sizeof(float2),
+                           "cudaMalloc(little operator inverse blocks)")) ||
         (rc = dalloc_bytes((void**)&lc, nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
         (rc = dalloc_bytes((void**)&d_bad, sizeof(int), "cudaMalloc(deflation status)")) ||
         (rc = dalloc_bytes((void**)&lstate, sizeof(LittleState), "cudaMalloc(little solver state)")))
@@ -457,6 +461,7 @@ int DflWork::ensure(const Geom& g, int ns_) {
             return rc;
     if ((rc = red.init())) return rc;
     ns = ns_;
+    eo = ns == 8 || ns == 16 || ns == 32;  // the warp-per-block kernels
     return QXD_OK;
 }
 
@@ -481,6 +486,9 @@ int orthonormalise(qxd_lattice* lat, DflWork& W, cudaStream_t st) {
     return QXD_OK;
 }
 
+template <int NS>
+void launch_invert(DflWork& W, cudaStream_t st);  // A_oo^-1 of the odd blocks (defined with the little solver)
+
 int build_little(qxd_lattice* lat, DflWork& W, cudaStream_t st) {
     const Geom& g = lat->g;
     Fields<float> f{nullptr, nullptr, lat->U32, lat->A32, lat->C32};
@@ -494,6 +502,17 @@ int build_little(qxd_lattice* lat, DflWork& W, cudaStream_t st) {
         QXD_LAUNCHED("k_dfl_faces");
         k_dfl_project<<<W.d.nblk, BSITES, 0, st>>>(g, W.d, W.ns, l, W.basis, W.tfield, W.H, W.A);
         QXD_LAUNCHED("k_dfl_project");
+    }
+    if (W.eo) {  // inverse self-couplings of the odd blocks
+        QXD_CUDA(cudaMemsetAsync(W.d_bad, 0, sizeof(int), st));
+        if (W.ns == 16) launch_invert<16>(W, st);
+        else if (W.ns == 8) launch_invert<8>(W, st);
+        else launch_invert<32>(W, st);
+        QXD_LAUNCHED("k_lt_invert");
+        int bad = 0;
+        QXD_CUDA(cudaMemcpyAsync(&bad, W.d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+        QXD_CUDA(cudaStreamSynchronize(st));
+        if (bad) return fail(QXD_ERR_NUMERIC, "little operator: singular self-coupling of an odd block");
     }
     QXD_CUDA(cudaStreamSynchronize(st));
     W.op_version = lat->op_version;
@@ -752,11 +771,305 @@ __global__ void k_lt_init(size_t n, const double2* __restrict__ c, float2* __res
         r[i] = make_float2((float)c[i].x, (float)c[i].y);
 }
 
+// ---------------------------------------------------------------------------
+// Even-odd form of the little system. Blocks of one colour (parity of the
+// block coordinates, as in the Schwarz method) couple only to blocks of the
+// other colour, so with A_ee, A_oo the self-couplings
+//   A_hat = A_ee - A_eo A_oo^-1 A_oe   on the even blocks,
+//   A_hat y_e = c_e - A_eo A_oo^-1 c_o,  y_o = A_oo^-1 (c_o - A_oe y_e).
+// The GCR runs on A_hat (full-length vectors whose odd entries stay zero).
+// One warp per block, lanes as in k_lt_apply_warp; A_oo^-1 is formed once per
+// little operator by Gauss-Jordan elimination in FP64.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int block_parity(const DflGeom& d, int b) {
+    const int B3 = b % d.nb[3];
+    int r = b / d.nb[3];
+    const int B2 = r % d.nb[2];
+    r /= d.nb[2];
+    const int B1 = r % d.nb[1];
+    const int B0 = r / d.nb[1];
+    return (B0 + B1 + B2 + B3) & 1;
+}
+
+// block number i of parity p (blocks 2i and 2i + 1 differ only in B3, and
+// nb[3] is even, so one of them has each parity)
+__device__ __forceinline__ int block_of_parity(const DflGeom& d, int i, int p) {
+    const int b = 2 * i;
+    return block_parity(d, b) == p ? b : b + 1;
+}
+
+__device__ __forceinline__ float2 to_f2(float2 v) { return v; }
+__device__ __forceinline__ float2 to_f2(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
+// this lane's share of row k of sum_{j = j0 .. j1} A[b][j] v[n_j(b)]
+template <int NS, typename T>
+__device__ __forceinline__ void lt_rows(const Geom& g, const DflGeom& d, const float2* __restrict__ A,
+                                       const T* __restrict__ v, int b, int j0, int j1, int k, int part, float& re,
+                                       float& im) {
+    constexpr int G = 32 / NS, CH = NS / G;
+#pragma unroll 1
+    for (int j = j0; j <= j1; ++j) {
+        const int nb = j == 0 ? b : block_nbr(g, d, b, (j - 1) >> 1, (j & 1) ? +1 : -1);
+        const float2* a = A + (((size_t)b * 9 + j) * NS + k) * NS + part * CH;
+        const T* x = v + (size_t)nb * NS + part * CH;
+#pragma unroll
+        for (int l = 0; l < CH; ++l) {
+            const float2 al = __ldcs(a + l), vl = to_f2(x[l]);
+            re = fmaf(al.x, vl.x, fmaf(-al.y, vl.y, re));
+            im = fmaf(al.x, vl.y, fmaf(al.y, vl.x, im));
+        }
+    }
+}
+
+// sum of a row over its G lanes (every lane of the row gets it)
+template <int NS>
+__device__ __forceinline__ void row_sum(float& re, float& im) {
+#pragma unroll
+    for (int o = (32 / NS) / 2; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+}
+
+// y = A_oo^-1[b] u with u_k given by the lanes of row k (part 0 holds it);
+// returns row k of y in every lane of the row
+template <int NS>
+__device__ __forceinline__ float2 apply_inv(const float2* __restrict__ Ainv, int b, float2 uk, int k, int part,
+                                            float2* su) {
+    constexpr int G = 32 / NS, CH = NS / G;
+    if (part == 0) su[k] = uk;
+    __syncwarp();
+    const float2* a = Ainv + ((size_t)b * NS + k) * NS + part * CH;
+    float re = 0.f, im = 0.f;
+#pragma unroll
+    for (int l = 0; l < CH; ++l) {
+        const float2 al = a[l], vl = su[part * CH + l];
+        re = fmaf(al.x, vl.x, fmaf(-al.y, vl.y, re));
+        im = fmaf(al.x, vl.y, fmaf(al.y, vl.x, im));
+    }
+    row_sum<NS>(re, im);
+    __syncwarp();
+    return make_float2(re, im);
+}
+
+// A_oo^-1 for the odd blocks: Gauss-Jordan with partial pivoting on [A_bb | 1]
+// in FP64 shared memory, one warp per odd block; a pivot below 1e-12 of the
+// largest entry of the block (or not finite) flags the block as singular
+template <int NS>
+__global__ void __launch_bounds__(32) k_lt_invert(DflGeom d, const float2* __restrict__ A, float2* __restrict__ Ainv,
+                                                  int* __restrict__ bad) {
+    __shared__ double2 M[NS][2 * NS];
+    __shared__ double2 f[NS];
+    const int b = block_of_parity(d, blockIdx.x, 1);
+    const int lane = threadIdx.x;
+    const float2* a = A + (size_t)b * 9 * NS * NS;  // j = 0: the self-coupling
+    double amax = 0.0;
+    for (int e = lane; e < NS * 2 * NS; e += 32) {
+        const int r = e / (2 * NS), c = e % (2 * NS);
+        double2 v = make_double2(r == c - NS ? 1.0 : 0.0, 0.0);
+        if (c < NS) {
+            const float2 x = a[r * NS + c];
+            v = make_double2(x.x, x.y);
+            amax = fmax(amax, fabs(v.x) + fabs(v.y));
+        }
+        M[r][c] = v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    __syncwarp();
+    bool ok = true;
+    for (int c = 0; c < NS; ++c) {
+        // pivot: largest |M[r][c]| over r >= c (lowest row on ties)
+        double best = -1.0;
+        int pr = c;
+        for (int r = c + lane; r < NS; r += 32) {
+            const double m = fabs(M[r][c].x) + fabs(M[r][c].y);
+            if (m > best) {
+                best = m;
+                pr = r;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int opr = __shfl_xor_sync(0xffffffffu, pr, o);
+            if (ob > best || (ob == best && opr < pr)) {
+                best = ob;
+                pr = opr;
+            }
+        }
+        if (!(best > 1e-12 * amax) || !isfinite(best)) {
+            ok = false;
+            break;
+        }
+        for (int e = lane; e < 2 * NS; e += 32) {  // swap rows c and pr
+            const double2 t = M[c][e];
+            M[c][e] = M[pr][e];
+            M[pr][e] = t;
+        }
+        __syncwarp();
+        const double2 pv = M[c][c];
+        const double den = pv.x * pv.x + pv.y * pv.y;
+        const double2 inv = make_double2(pv.x / den, -pv.y / den);
+        __syncwarp();
+        for (int e = lane; e < 2 * NS; e += 32) {  // row c /= pivot
+            const double2 t = M[c][e];
+            M[c][e] = make_double2(t.x * inv.x - t.y * inv.y, t.x * inv.y + t.y * inv.x);
+        }
+        for (int r = lane; r < NS; r += 32) f[r] = M[r][c];
+        __syncwarp();
+        for (int e = lane; e < NS * 2 * NS; e += 32) {  // row r -= f_r row c, r != c
+            const int r = e / (2 * NS), cc = e % (2 * NS);
+            if (r == c) continue;
+            const double2 fr = f[r], mc = M[c][cc];
+            M[r][cc] = make_double2(M[r][cc].x - (fr.x * mc.x - fr.y * mc.y), M[r][cc].y - (fr.x * mc.y + fr.y * mc.x));
+        }
+        __syncwarp();
+    }
+    if (!ok) {
+        if (lane == 0) atomicAdd(bad, 1);
+        return;
+    }
+    float2* out = Ainv + (size_t)b * NS * NS;
+    for (int e = lane; e < NS * NS; e += 32) {
+        const double2 v = M[e / NS][NS + e % NS];
+        out[e] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// Schur apply, odd half: t_o = A_oo^-1 (A_oe r_e); p_o = q_o = 0
+template <int NS>
+__global__ void __launch_bounds__(32) k_lt_schur_odd(Geom g, DflGeom d, const float2* __restrict__ A,
+                                                     const float2* __restrict__ Ainv, const float2* __restrict__ r,
+                                                     float2* __restrict__ t, float2* __restrict__ p,
+                                                     float2* __restrict__ q, const LittleState* __restrict__ S) {
+    if (S->done) return;
+    __shared__ float2 su[NS];
+    constexpr int G = 32 / NS;
+    const int b = block_of_parity(d, blockIdx.x, 1), lane = threadIdx.x;
+    const int k = lane / G, part = lane % G;
+    float re = 0.f, im = 0.f;
+    lt_rows<NS>(g, d, A, r, b, 1, 8, k, part, re, im);
+    row_sum<NS>(re, im);
+    const float2 y = apply_inv<NS>(Ainv, b, make_float2(re, im), k, part, su);
+    if (part == 0) {
+        const size_t i = (size_t)b * NS + k;
+        t[i] = y;
+        p[i] = make_float2(0.f, 0.f);
+        q[i] = make_float2(0.f, 0.f);
+    }
+}
+
+// Schur apply, even half: q_e = A_ee r_e - A_eo t_o; p_e = r_e
+template <int NS>
+__global__ void __launch_bounds__(32) k_lt_schur_even(Geom g, DflGeom d, const float2* __restrict__ A,
+                                                      const float2* __restrict__ r, const float2* __restrict__ t,
+                                                      float2* __restrict__ p, float2* __restrict__ q,
+                                                      const LittleState* __restrict__ S) {
+    if (S->done) return;
+    constexpr int G = 32 / NS;
+    const int b = block_of_parity(d, blockIdx.x, 0), lane = threadIdx.x;
+    const int k = lane / G, part = lane % G;
+    float re = 0.f, im = 0.f, he = 0.f, hm = 0.f;
+    lt_rows<NS>(g, d, A, r, b, 0, 0, k, part, re, im);
+    lt_rows<NS>(g, d, A, t, b, 1, 8, k, part, he, hm);
+    re -= he;
+    im -= hm;
+    row_sum<NS>(re, im);
+    if (part == 0) {
+        const size_t i = (size_t)b * NS + k;
+        q[i] = make_float2(re, im);
+        p[i] = r[i];
+    }
+}
+
+// source of the Schur system, odd half: t_o = A_oo^-1 c_o, r_o = 0
+template <int NS>
+__global__ void __launch_bounds__(32) k_lt_prep_odd(DflGeom d, const float2* __restrict__ Ainv,
+                                                    const double2* __restrict__ c, float2* __restrict__ t,
+                                                    float2* __restrict__ r) {
+    __shared__ float2 su[NS];
+    constexpr int G = 32 / NS;
+    const int b = block_of_parity(d, blockIdx.x, 1), lane = threadIdx.x;
+    const int k = lane / G, part = lane % G;
+    const size_t i = (size_t)b * NS + k;
+    const float2 y = apply_inv<NS>(Ainv, b, to_f2(c[i]), k, part, su);
+    if (part == 0) {
+        t[i] = y;
+        r[i] = make_float2(0.f, 0.f);
+    }
+}
+
+// even half: r_e = c_e - A_eo t_o
+template <int NS>
+__global__ void __launch_bounds__(32) k_lt_prep_even(Geom g, DflGeom d, const float2* __restrict__ A,
+                                                     const double2* __restrict__ c, const float2* __restrict__ t,
+                                                     float2* __restrict__ r) {
+    constexpr int G = 32 / NS;
+    const int b = block_of_parity(d, blockIdx.x, 0), lane = threadIdx.x;
+    const int k = lane / G, part = lane % G;
+    float re = 0.f, im = 0.f;
+    lt_rows<NS>(g, d, A, t, b, 1, 8, k, part, re, im);
+    row_sum<NS>(re, im);
+    if (part == 0) {
+        const size_t i = (size_t)b * NS + k;
+        const float2 ci = to_f2(c[i]);
+        r[i] = make_float2(ci.x - re, ci.y - im);
+    }
+}
+
+// solution on the odd blocks: x_o = A_oo^-1 (c_o - A_oe x_e)
+template <int NS>
+__global__ void __launch_bounds__(32) k_lt_recon_odd(Geom g, DflGeom d, const float2* __restrict__ A,
+                                                     const float2* __restrict__ Ainv, const double2* __restrict__ c,
+                                                     double2* __restrict__ x) {
+    __shared__ float2 su[NS];
+    constexpr int G = 32 / NS;
+    const int b = block_of_parity(d, blockIdx.x, 1), lane = threadIdx.x;
+    const int k = lane / G, part = lane % G;
+    float re = 0.f, im = 0.f;
+    lt_rows<NS>(g, d, A, x, b, 1, 8, k, part, re, im);
+    row_sum<NS>(re, im);
+    const size_t i = (size_t)b * NS + k;
+    const float2 ci = to_f2(c[i]);
+    const float2 y = apply_inv<NS>(Ainv, b, make_float2(ci.x - re, ci.y - im), k, part, su);
+    if (part == 0) x[i] = make_double2(y.x, y.y);
+}
+
+template <int NS>
+void launch_schur(qxd_lattice* lat, DflWork& W, int k, cudaStream_t st) {
+    const int nh = W.d.nblk / 2;
+    k_lt_schur_odd<NS><<<nh, 32, 0, st>>>(lat->g, W.d, W.A, W.Ainv, W.lr, W.lt, W.lp[k], W.lq[k], W.lstate);
+    k_lt_schur_even<NS><<<nh, 32, 0, st>>>(lat->g, W.d, W.A, W.lr, W.lt, W.lp[k], W.lq[k], W.lstate);
+}
+
+template <int NS>
+void launch_prep(qxd_lattice* lat, DflWork& W, cudaStream_t st) {
+    const int nh = W.d.nblk / 2;
+    k_lt_prep_odd<NS><<<nh, 32, 0, st>>>(W.d, W.Ainv, W.lc, W.lt, W.lr);
+    k_lt_prep_even<NS><<<nh, 32, 0, st>>>(lat->g, W.d, W.A, W.lc, W.lt, W.lr);
+}
+
+template <int NS>
+void launch_recon(qxd_lattice* lat, DflWork& W, cudaStream_t st) {
+    k_lt_recon_odd<NS><<<W.d.nblk / 2, 32, 0, st>>>(lat->g, W.d, W.A, W.Ainv, W.lc, W.lx);
+}
+
+template <int NS>
+void launch_invert(DflWork& W, cudaStream_t st) {
+    k_lt_invert<NS><<<W.d.nblk / 2, 32, 0, st>>>(W.d, W.A, W.Ainv, W.d_bad);
+}
+
 // the launches of one restart cycle (steps k = 0 .. DFL_NKV - 1)
 void little_cycle(qxd_lattice* lat, DflWork& W, cudaStream_t st) {
     const size_t n = (size_t)W.d.nblk * W.ns;
     for (int k = 0; k < DFL_NKV; ++k) {
-        if (W.ns == 16)
+        if (W.eo) {
+            if (W.ns == 16) launch_schur<16>(lat, W, k, st);
+            else if (W.ns == 8) launch_schur<8>(lat, W, k, st);
+            else launch_schur<32>(lat, W, k, st);
+        } else if (W.ns == 16)
             k_lt_apply_warp<16><<<W.d.nblk, 32, 0, st>>>(lat->g, W.d, W.A, W.lr, W.lp[k], W.lq[k], W.lstate);
         else if (W.ns == 8)
             k_lt_apply_warp<8><<<W.d.nblk, 32, 0, st>>>(lat->g, W.d, W.A, W.lr, W.lp[k], W.lq[k], W.lstate);
@@ -809,35 +1122,52 @@ int little_cycle_graph(qxd_lattice* lat, DflWork& W) {
     return QXD_OK;
 }
 
-// GCR on the little system A y = c (W.lc) into W.lx, to |r| <= tol |c| or
-// max_iter steps (restarted every DFL_NKV steps)
+// GCR on the little system A y = c (W.lc) into W.lx, restarted every
+// DFL_NKV steps, to |r| <= tol |c| or max_iter steps. With W.eo the GCR runs
+// on the Schur complement of the even blocks (|r| and c of that system), and
+// the odd blocks follow from the even ones.
 int little_gcr(qxd_lattice* lat, DflWork& W, double tol, int max_iter, int* iters, cudaStream_t st) {
     const size_t n = (size_t)W.d.nblk * W.ns;
     const size_t bytes = n * sizeof(double2);
     int rc;
-    double cc;
-    if ((rc = blas_norm2<double2>(W.red, n, W.lc, &cc, st))) return rc;
     QXD_CUDA(cudaMemsetAsync(W.lx, 0, bytes, st));
-    *iters = 0;
-    if (cc == 0.0) return QXD_OK;
-    if (!std::isfinite(cc)) return fail(QXD_ERR_NUMERIC, "little solver: non-finite source");
-    k_lt_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, W.lc, W.lr);
-    QXD_LAUNCHED("k_lt_init");
-    LittleState& h = *W.h_lstate;
-    h = LittleState{};
-    h.rn2 = cc;
-    h.target2 = tol * tol * cc;
-    h.max_iter = max_iter;
-    h.done = (max_iter < 1 || tol >= 1.0) ? 1 : 0;
-    QXD_CUDA(cudaMemcpyAsync(W.lstate, &h, sizeof(LittleState), cudaMemcpyHostToDevice, st));
-    if ((rc = little_cycle_graph(lat, W))) return rc;
-    while (!h.done) {
-        QXD_CUDA(cudaGraphLaunch(W.cycle, st));
-        QXD_CUDA(cudaMemcpyAsync(&h, W.lstate, sizeof(LittleState), cudaMemcpyDeviceToHost, st));
-        QXD_CUDA(cudaStreamSynchronize(st));
+    double cc;
+    if (W.eo) {
+        if (W.ns == 16) launch_prep<16>(lat, W, st);
+        else if (W.ns == 8) launch_prep<8>(lat, W, st);
+        else launch_prep<32>(lat, W, st);
+        QXD_LAUNCHED("k_lt_prep");
+        if ((rc = blas_norm2<float2>(W.red, n, W.lr, &cc, st))) return rc;
+    } else {
+        if ((rc = blas_norm2<double2>(W.red, n, W.lc, &cc, st))) return rc;
+        k_lt_init<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, W.lc, W.lr);
+        QXD_LAUNCHED("k_lt_init");
     }
-    if (h.status) return fail(QXD_ERR_NUMERIC, "little solver: breakdown or non-finite residual");
-    *iters = h.it;
+    *iters = 0;
+    if (!std::isfinite(cc)) return fail(QXD_ERR_NUMERIC, "little solver: non-finite source");
+    if (cc > 0.0) {
+        LittleState& h = *W.h_lstate;
+        h = LittleState{};
+        h.rn2 = cc;
+        h.target2 = tol * tol * cc;
+        h.max_iter = max_iter;
+        h.done = (max_iter < 1 || tol >= 1.0) ? 1 : 0;
+        QXD_CUDA(cudaMemcpyAsync(W.lstate, &h, sizeof(LittleState), cudaMemcpyHostToDevice, st));
+        if ((rc = little_cycle_graph(lat, W))) return rc;
+        while (!h.done) {
+            QXD_CUDA(cudaGraphLaunch(W.cycle, st));
+            QXD_CUDA(cudaMemcpyAsync(&h, W.lstate, sizeof(LittleState), cudaMemcpyDeviceToHost, st));
+            QXD_CUDA(cudaStreamSynchronize(st));
+        }
+        if (h.status) return fail(QXD_ERR_NUMERIC, "little solver: breakdown or non-finite residual");
+        *iters = h.it;
+    }
+    if (W.eo) {  // x_o = A_oo^-1 (c_o - A_oe x_e)
+        if (W.ns == 16) launch_recon<16>(lat, W, st);
+        else if (W.ns == 8) launch_recon<8>(lat, W, st);
+        else launch_recon<32>(lat, W, st);
+        QXD_LAUNCHED("k_lt_recon_odd");
+    }
     return QXD_OK;
 }
 

@@ -36,6 +36,9 @@ struct DflWork {
     float4* H = nullptr;       // [4] face hops (FP32 fields)
     double2 *lx = nullptr, *lc = nullptr;  // little solution and source [nblk * ns] (FP64)
     float2* lr = nullptr;                  // little residual (FP32)
+    float2* lt = nullptr;                  // even-odd work vector (FP32)
+    float2* Ainv = nullptr;                // [nblk][ns][ns]: inverse self-coupling of the odd blocks
+    bool eo = false;                       // little solve on the even blocks (Schur complement)
     float2* lp[DFL_NKV] = {};              // little Krylov vectors (FP32)
     float2* lq[DFL_NKV] = {};
     int* d_bad = nullptr;
