@@ -26,7 +26,6 @@ __device__ __forceinline__ double2 ld(const float2* p, size_t i) {
     return make_double2(v.x, v.y);
 }
 __device__ __forceinline__ double2 ld(const double2* p, size_t i) { return p[i]; }
-__device__ __forceinline__ void st_(float2* p, size_t i, double2 v) { p[i] = make_float2((float)v.x, (float)v.y); }
 __device__ __forceinline__ void st_(double2* p, size_t i, double2 v) { p[i] = v; }
 
 __global__ void __launch_bounds__(RED_FINAL_THREADS) k_reduce_final(const double* __restrict__ partials, int nc,
@@ -37,86 +36,22 @@ __global__ void __launch_bounds__(RED_FINAL_THREADS) k_reduce_final(const double
     }
 }
 
-// out[j] += conj(x_j[i]) y[i] for the elements i of this thread, FP32 runs
-// added to FP64 sums (the FP32 form of the multi-dot)
-__device__ __forceinline__ void mdot_f32(size_t n, int k, const float2* const* xs, const float2* __restrict__ y,
-                                         double acc[2 * BLAS_KMAX]) {
-    float run[2 * BLAS_KMAX];
-#pragma unroll
-    for (int c = 0; c < 2 * BLAS_KMAX; ++c) run[c] = 0.f;
-    int cnt = 0;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float2 b = y[i];
-#pragma unroll
-        for (int j = 0; j < BLAS_KMAX; ++j) {
-            if (j >= k) break;
-            const float2 a = xs[j][i];
-            run[2 * j] = fmaf(a.x, b.x, fmaf(a.y, b.y, run[2 * j]));
-            run[2 * j + 1] = fmaf(a.x, b.y, fmaf(-a.y, b.x, run[2 * j + 1]));
-        }
-        if (++cnt == RUN) {
-#pragma unroll
-            for (int c = 0; c < 2 * BLAS_KMAX; ++c) {
-                acc[c] += run[c];
-                run[c] = 0.f;
-            }
-            cnt = 0;
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 2 * BLAS_KMAX; ++c) acc[c] += run[c];
-}
-
-// y -= sum_j c_j x_j in FP32 for the elements of this thread; acc[0] += |y|^2
-// (FP32 runs added to the FP64 sum)
-__device__ __forceinline__ void maxpy_norm_f32(size_t n, int k, const double* cre, const double* cim,
-                                               const float2* const* xs, float2* __restrict__ y, double* acc) {
-    float cr[BLAS_KMAX], ci[BLAS_KMAX];
-#pragma unroll
-    for (int j = 0; j < BLAS_KMAX; ++j) {
-        cr[j] = j < k ? (float)cre[j] : 0.f;
-        ci[j] = j < k ? (float)cim[j] : 0.f;
-    }
-    float run = 0.f;
-    int cnt = 0;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        float2 b = y[i];
-#pragma unroll
-        for (int j = 0; j < BLAS_KMAX; ++j) {
-            if (j >= k) break;
-            const float2 a = xs[j][i];
-            b.x = fmaf(-cr[j], a.x, fmaf(ci[j], a.y, b.x));
-            b.y = fmaf(-cr[j], a.y, fmaf(-ci[j], a.x, b.y));
-        }
-        y[i] = b;
-        run = fmaf(b.x, b.x, fmaf(b.y, b.y, run));
-        if (++cnt == RUN) {
-            acc[0] += run;
-            run = 0.f;
-            cnt = 0;
-        }
-    }
-    acc[0] += run;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_mdot(size_t n, int k, VecList<T> xs, const T* __restrict__ y,
                                                       double* __restrict__ partials) {
+    // FP64 vectors (the FP32 form is k_mdot32)
     double acc[2 * BLAS_KMAX];
 #pragma unroll
     for (int c = 0; c < 2 * BLAS_KMAX; ++c) acc[c] = 0.0;
-    if constexpr (is_f32<T>()) {
-        mdot_f32(n, k, xs.p, y, acc);
-    } else {
-        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-            const double2 b = ld(y, i);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 b = ld(y, i);
 #pragma unroll
-            for (int j = 0; j < BLAS_KMAX; ++j) {
-                if (j >= k) break;
-                const double2 a = ld(xs.p[j], i);
-                acc[2 * j] += a.x * b.x + a.y * b.y;
-                acc[2 * j + 1] += a.x * b.y - a.y * b.x;
-            }
+        for (int j = 0; j < BLAS_KMAX; ++j) {
+            if (j >= k) break;
+            const double2 a = ld(xs.p[j], i);
+            acc[2 * j] += a.x * b.x + a.y * b.y;
+            acc[2 * j + 1] += a.x * b.y - a.y * b.x;
         }
     }
     block_reduce_store<2 * BLAS_KMAX>(acc, 2 * k, partials);
@@ -269,12 +204,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_norm2(size_t n, const T* __rest
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_maxpy_norm(size_t n, int k, CoefList c, VecList<T> xs,
                                                             T* __restrict__ y, double* __restrict__ partials) {
+    // FP64 vectors (the FP32 form is k_maxpy_norm32)
     double acc[1] = {0.0};
-    if constexpr (is_f32<T>()) {
-        maxpy_norm_f32(n, k, c.re, c.im, xs.p, y, acc);
-        block_reduce_store<1>(acc, 1, partials);
-        return;
-    }
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         double2 b = ld(y, i);
 #pragma unroll
@@ -302,14 +233,14 @@ __global__ void k_caxpy(size_t n, double cre, double cim, const T* __restrict__ 
             b.y = fmaf(-cr, a.y, fmaf(-ci, a.x, b.y));
             y[i] = b;
         }
-        return;
-    }
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const double2 a = ld(x, i);
-        double2 b = ld(y, i);
-        b.x -= cre * a.x - cim * a.y;
-        b.y -= cre * a.y + cim * a.x;
-        st_(y, i, b);
+    } else {
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+            const double2 a = ld(x, i);
+            double2 b = ld(y, i);
+            b.x -= cre * a.x - cim * a.y;
+            b.y -= cre * a.y + cim * a.x;
+            st_(y, i, b);
+        }
     }
 }
 
@@ -321,13 +252,13 @@ __global__ void k_scale(size_t n, double s, T* __restrict__ x) {
             const float2 a = x[i];
             x[i] = make_float2(a.x * sf, a.y * sf);
         }
-        return;
-    }
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        double2 a = ld(x, i);
-        a.x *= s;
-        a.y *= s;
-        st_(x, i, a);
+    } else {
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+            double2 a = ld(x, i);
+            a.x *= s;
+            a.y *= s;
+            st_(x, i, a);
+        }
     }
 }
 
@@ -592,6 +523,183 @@ __device__ __forceinline__ void block_reduce_store_at(double* v, int nc, double*
     }
 }
 
+// block-wide sum of NC values per thread into part[0 .. NC) (this block's row)
+template <int NC>
+__device__ __forceinline__ void block_reduce_row(const double v[NC], double* __restrict__ part,
+                                                 double (*sh)[2 * BLAS_KMAX]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        double x = v[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[warp][c] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NC) {
+        double x = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) x += sh[w][threadIdx.x];
+        part[threadIdx.x] = x;
+    }
+    __syncthreads();  // sh is reused by the next pass
+}
+
+// Batched FP32 multi-dot and multi-axpy. Each job is taken in passes of at
+// most 8 vectors with the vector count fixed at compile time, chosen by the
+// job's own count: a job's element order and run lengths do not depend on
+// the other jobs of the batch, so a request gives the same bits alone and
+// in a mix.
+
+// <x_j, y> for K vectors of one job into part[0 .. 2K)
+template <int K>
+__device__ __forceinline__ void mdot_pass32(size_t n, const void* const* xsv, const float2* __restrict__ y,
+                                            double* part, double (*sh)[2 * BLAS_KMAX]) {
+    constexpr int U = elems_per_iter<K>();
+    const float2* xs[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) xs[j] = (const float2*)xsv[j];
+    float run[2 * K];
+    double acc[2 * K];
+#pragma unroll
+    for (int c = 0; c < 2 * K; ++c) {
+        run[c] = 0.f;
+        acc[c] = 0.0;
+    }
+    int cnt = 0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
+        float2 b[U], a[U][K];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t i = i0 + u * stride;
+            b[u] = i < n ? y[i] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < K; ++j) a[u][j] = i < n ? xs[j][i] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                run[2 * j] = fmaf(a[u][j].x, b[u].x, fmaf(a[u][j].y, b[u].y, run[2 * j]));
+                run[2 * j + 1] = fmaf(a[u][j].x, b[u].y, fmaf(-a[u][j].y, b[u].x, run[2 * j + 1]));
+            }
+        if ((cnt += U) >= RUN) {
+#pragma unroll
+            for (int c = 0; c < 2 * K; ++c) {
+                acc[c] += run[c];
+                run[c] = 0.f;
+            }
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 2 * K; ++c) acc[c] += run[c];
+    block_reduce_row<2 * K>(acc, part, sh);
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_blas_mdot32(const BJob* __restrict__ jobs,
+                                                             double* __restrict__ partials) {
+    __shared__ double sh[RED_THREADS / 32][2 * BLAS_KMAX];
+    const BJob& J = jobs[blockIdx.y];
+    double* part = partials + ((size_t)blockIdx.y * RED_BLOCKS + blockIdx.x) * 2 * BLAS_KMAX;
+    const float2* y = (const float2*)J.y;
+    for (int j0 = 0; j0 < J.k; j0 += 8) {
+        const void* const* xs = J.xs + j0;
+        double* p = part + 2 * j0;
+        switch (J.k - j0 < 8 ? J.k - j0 : 8) {
+            case 1: mdot_pass32<1>(J.n, xs, y, p, sh); break;
+            case 2: mdot_pass32<2>(J.n, xs, y, p, sh); break;
+            case 3: mdot_pass32<3>(J.n, xs, y, p, sh); break;
+            case 4: mdot_pass32<4>(J.n, xs, y, p, sh); break;
+            case 5: mdot_pass32<5>(J.n, xs, y, p, sh); break;
+            case 6: mdot_pass32<6>(J.n, xs, y, p, sh); break;
+            case 7: mdot_pass32<7>(J.n, xs, y, p, sh); break;
+            default: mdot_pass32<8>(J.n, xs, y, p, sh); break;
+        }
+    }
+}
+
+// y -= sum_j c_j x_j for K vectors of one job; with `norm`, returns this
+// thread's |y|^2 (FP32 runs added in FP64)
+template <int K>
+__device__ __forceinline__ double maxpy_pass32(size_t n, const void* const* xsv, const double* cre,
+                                               const double* cim, float2* __restrict__ y, bool norm) {
+    constexpr int U = elems_per_iter<K>();
+    constexpr int KA = K > 0 ? K : 1;
+    const float2* xs[KA];
+    float cr[KA], ci[KA];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        xs[j] = (const float2*)xsv[j];
+        cr[j] = (float)cre[j];
+        ci[j] = (float)cim[j];
+    }
+    float run = 0.f;
+    double acc = 0.0;
+    int cnt = 0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
+        float2 b[U], a[U][KA];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t i = i0 + u * stride;
+            b[u] = i < n ? y[i] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < K; ++j) a[u][j] = i < n ? xs[j][i] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const size_t i = i0 + u * stride;
+            if (i >= n) continue;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                b[u].x = fmaf(-cr[j], a[u][j].x, fmaf(ci[j], a[u][j].y, b[u].x));
+                b[u].y = fmaf(-cr[j], a[u][j].y, fmaf(-ci[j], a[u][j].x, b[u].y));
+            }
+            if (K > 0) y[i] = b[u];
+            run = fmaf(b[u].x, b[u].x, fmaf(b[u].y, b[u].y, run));
+        }
+        if ((cnt += U) >= RUN) {
+            acc += run;
+            run = 0.f;
+            cnt = 0;
+        }
+    }
+    return norm ? acc + run : 0.0;
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_blas_maxpy32(const BJob* __restrict__ jobs,
+                                                              double* __restrict__ partials) {
+    __shared__ double sh[RED_THREADS / 32][2 * BLAS_KMAX];
+    const BJob& J = jobs[blockIdx.y];
+    double* part = partials + ((size_t)blockIdx.y * RED_BLOCKS + blockIdx.x) * 2 * BLAS_KMAX;
+    float2* y = (float2*)J.out;
+    double acc[1] = {0.0};
+    for (int j0 = 0;; j0 += 8) {  // passes of up to 8 vectors; |y|^2 in the last
+        const int kk = J.k - j0 < 8 ? J.k - j0 : 8;
+        const bool last = j0 + kk >= J.k;
+        const void* const* xs = J.xs + j0;
+        const double *cr = J.cre + j0, *ci = J.cim + j0;
+        double a = 0.0;
+        switch (kk) {
+            case 0: a = maxpy_pass32<0>(J.n, xs, cr, ci, y, last); break;
+            case 1: a = maxpy_pass32<1>(J.n, xs, cr, ci, y, last); break;
+            case 2: a = maxpy_pass32<2>(J.n, xs, cr, ci, y, last); break;
+            case 3: a = maxpy_pass32<3>(J.n, xs, cr, ci, y, last); break;
+            case 4: a = maxpy_pass32<4>(J.n, xs, cr, ci, y, last); break;
+            case 5: a = maxpy_pass32<5>(J.n, xs, cr, ci, y, last); break;
+            case 6: a = maxpy_pass32<6>(J.n, xs, cr, ci, y, last); break;
+            case 7: a = maxpy_pass32<7>(J.n, xs, cr, ci, y, last); break;
+            default: a = maxpy_pass32<8>(J.n, xs, cr, ci, y, last); break;
+        }
+        if (last) {
+            acc[0] = a;
+            break;
+        }
+    }
+    block_reduce_row<1>(acc, part, sh);
+}
+
 // one kernel for all batched operations; the switch is uniform per launch
 __global__ void __launch_bounds__(RED_THREADS) k_blas_batch(int op, const BJob* __restrict__ jobs,
                                                             double* __restrict__ partials) {
@@ -599,18 +707,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_blas_batch(int op, const BJob* 
     double* part = partials + ((size_t)blockIdx.y * RED_BLOCKS + blockIdx.x) * 2 * BLAS_KMAX;
     const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t step = (size_t)gridDim.x * blockDim.x;
-    if (op == B_MDOT_F32) {
-        // the same arithmetic as k_mdot<float2>, per job
-        double acc[2 * BLAS_KMAX];
-#pragma unroll
-        for (int c = 0; c < 2 * BLAS_KMAX; ++c) acc[c] = 0.0;
-        mdot_f32(J.n, J.k, (const float2* const*)J.xs, (const float2*)J.y, acc);
-        block_reduce_store_at(acc, 2 * J.k, part);
-    } else if (op == B_MAXPY_NORM_F32) {
-        double acc[1] = {0.0};
-        maxpy_norm_f32(J.n, J.k, J.cre, J.cim, (const float2* const*)J.xs, (float2*)J.out, acc);
-        block_reduce_store_at(acc, 1, part);
-    } else if (op == B_NORM2_F64) {
+    if (op == B_NORM2_F64) {
         double acc[1] = {0.0};
         const double2* x = (const double2*)J.y;
         for (size_t i = i0; i < J.n; i += step) acc[0] += x[i].x * x[i].x + x[i].y * x[i].y;
@@ -700,8 +797,16 @@ int blas_batch(BatchReducer& red, BOp op, int jobs, int nc, cudaStream_t st) {
         for (int j = 0; j < jobs; ++j) nmax = nmax > red.h_jobs[j].n ? nmax : red.h_jobs[j].n;
         grid.x = ew_blocks(nmax);
     }
-    k_blas_batch<<<grid, RED_THREADS, 0, st>>>((int)op, red.d_jobs, red.partials);
-    QXD_LAUNCHED("k_blas_batch");
+    if (op == B_MDOT_F32) {
+        k_blas_mdot32<<<grid, RED_THREADS, 0, st>>>(red.d_jobs, red.partials);
+        QXD_LAUNCHED("k_blas_mdot32");
+    } else if (op == B_MAXPY_NORM_F32) {
+        k_blas_maxpy32<<<grid, RED_THREADS, 0, st>>>(red.d_jobs, red.partials);
+        QXD_LAUNCHED("k_blas_maxpy32");
+    } else {
+        k_blas_batch<<<grid, RED_THREADS, 0, st>>>((int)op, red.d_jobs, red.partials);
+        QXD_LAUNCHED("k_blas_batch");
+    }
     if (!reduce) return QXD_OK;
     k_reduce_final_batch<<<jobs, RED_FINAL_THREADS, 0, st>>>(red.partials, nc, red.d_res);
     QXD_LAUNCHED("k_reduce_final_batch");
