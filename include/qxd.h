@@ -206,7 +206,10 @@ int qxd_sap(qxd_lattice* lat, void* out, const void* in, int ncy, int nmr, int f
  * inner_prec FP32; needs qxd_dfl_subspace, or qxd_dfl_refresh after the
  * operator changed): phi = chi + SAP(r - D chi), chi = P A^-1 P^dag r with the
  * little system A solved by GCR to a relative residual dfl_tol (at most
- * dfl_max_iter steps).
+ * dfl_max_iter steps). For ns = 8, 16 or 32 the GCR runs on the Schur
+ * complement of the even blocks (blocks coloured as in SAP), A_ee - A_eo
+ * A_oo^-1 A_oe, whose residual and source dfl_tol then refers to, and the
+ * odd blocks follow; for other ns on A itself.
  * ------------------------------------------------------------------------- */
 #define QXD_PRECOND_NONE 0
 #define QXD_PRECOND_SAP 1

@@ -447,9 +447,7 @@ int DflWork::ensure(const Geom& g, int ns_) {
         (rc = dalloc_bytes((void**)&H, 4 * 6 * V * sizeof(float4), "cudaMalloc(deflation faces)")) ||
         (rc = dalloc_bytes((void**)&lx, nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
         (rc = dalloc_bytes((void**)&lr, nl * sizeof(float2), "cudaMalloc(little vectors)")) ||
-        (rc = dalloc_bytes((void**)&lt, nl * sizeof(float2), "cudaMalloc(little vectors)")) ||
-        (rc = dalloc_bytes((void**)&Ainv, (size_t)d.nblk * ns_ * ns_ * sizeof(float2),
-                           "cudaMalloc(little operator inverse blocks)")) ||
+
         (rc = dalloc_bytes((void**)&lc, nl * sizeof(double2), "cudaMalloc(little vectors)")) ||
         (rc = dalloc_bytes((void**)&d_bad, sizeof(int), "cudaMalloc(deflation status)")) ||
         (rc = dalloc_bytes((void**)&lstate, sizeof(LittleState), "cudaMalloc(little solver state)")))
@@ -460,8 +458,12 @@ int DflWork::ensure(const Geom& g, int ns_) {
             (rc = dalloc_bytes((void**)&lq[k], nl * sizeof(float2), "cudaMalloc(little vectors)")))
             return rc;
     if ((rc = red.init())) return rc;
+    eo = ns_ == 8 || ns_ == 16 || ns_ == 32;  // the warp-per-block kernels
+    if (eo && ((rc = dalloc_bytes((void**)&lt, nl * sizeof(float2), "cudaMalloc(little vectors)")) ||
+               (rc = dalloc_bytes((void**)&Ainv, (size_t)d.nblk * ns_ * ns_ * sizeof(float2),
+                                  "cudaMalloc(little operator inverse blocks)"))))
+        return rc;
     ns = ns_;
-    eo = ns == 8 || ns == 16 || ns == 32;  // the warp-per-block kernels
     return QXD_OK;
 }
 
