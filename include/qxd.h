@@ -190,6 +190,20 @@ int qxd_eo_reconstruct(qxd_lattice* lat, void* x, const void* b, int flags, void
  */
 int qxd_sap(qxd_lattice* lat, void* out, const void* in, int ncy, int nmr, int flags, void* stream);
 
+/* out[i] = SAP(in[i]), i < nrhs: the FP32 Schwarz method of qxd_sap for
+ * nrhs right-hand sides of the same operator, solved together: each thread
+ * block stages the links of its block once and solves the block for each
+ * right-hand side in turn (the operator's links and clover blocks are read
+ * from DRAM once for all of them). Each out[i] is bit for bit the result of
+ * qxd_sap(lat, out[i], in[i], ncy, nmr, QXD_FP32 | QXD_LAYOUT_NATIVE).
+ * out and in: host arrays of nrhs device pointers to FP32 fields in the
+ * native layout (qxd_spinor_pack); every out[i] distinct and different from
+ * every in[j] (else QXD_ERR_ARG). The library keeps the work fields of nrhs
+ * right-hand sides (144 bytes per site each) with the lattice, reallocated
+ * when a call needs more, until qxd_lattice_destroy. Errors as for qxd_sap. */
+int qxd_sap_multi(qxd_lattice* lat, int nrhs, void* const* out, const void* const* in, int ncy, int nmr,
+                  void* stream);
+
 /* ---------------------------------------------------------------------------
  * Solver: D x = b to a true FP64 relative residual |b - D x| / |b| <= tol.
  * Flexible GCR (the paper names GCR with SAP preconditioning, Sec. 1-2, but

@@ -47,7 +47,7 @@ static int dalloc(T** p, size_t n, const char* what) {
 static void free_all(qxd_lattice* L) {
     release_hostio(L);
     void* own[] = {L->Zq64, L->C64, L->C32, L->Cinv64, L->Cinv32, L->d_status, L->scratch_in, L->scratch_out,
-                   L->scratch_lex, L->sap_r};
+                   L->scratch_lex, L->sap_r, L->sap_multi};
     for (void* p : own)
         if (p) cudaFree(p);
     if (L->parent) return;  // the gauge field belongs to the parent

@@ -17,6 +17,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "batch.cuh"
@@ -102,7 +103,7 @@ struct Job {
     // device vectors
     size_t f64_bytes = 0, f32_bytes = 0;
     void *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *t64 = nullptr, *rin = nullptr;
-    void* sapw = nullptr;  // work fields of the batched Schwarz solve (delta, rho of the even sites)
+    void* sapw = nullptr;  // work fields of the Schwarz solve (delta, rho of the even sites)
     size_t sapw_bytes = 0;
     void* phi[BLAS_KMAX] = {};
     void* chi[BLAS_KMAX] = {};
@@ -146,7 +147,6 @@ struct Engine {
     SapJob* d_sap = nullptr;
     int d_sap_cap = 0;
     SapGraphCache sap_graphs;  // graphs of the batched SAP launch sets
-    SapWork sap_single;  // geometry of the single-lattice Schwarz path
     long long steps = 0;
     size_t charged = 0;  // sum of the charges of the admitted requests
 
@@ -184,8 +184,7 @@ struct Engine {
         for (void** p : f64)
             if ((rc = pool.alloc(j->f64_bytes, p))) return rc;
         if ((rc = pool.alloc(j->f32_bytes, &j->rin))) return rc;
-        // the single-lattice Schwarz path keeps its work fields with the operator
-        if (j->P.precond == QXD_PRECOND_SAP && !big(j)) {
+        if (j->P.precond == QXD_PRECOND_SAP) {
             j->sapw_bytes = sap_work_bytes(j->op);
             if ((rc = pool.alloc(j->sapw_bytes, &j->sapw))) return rc;
         }
@@ -324,12 +323,13 @@ struct Engine {
                 if (n == 0) return QXD_OK;
             }
         }
-        // phi_k = P(rin)
+        // phi_k = P(rin); large lattices of one operator (and ncy, nmr) solved
+        // together, each thread block staging its links once for all of them
         std::vector<SapJob> sj;
+        std::map<std::tuple<qxd_lattice*, int, int>, std::vector<Job*>> same_op;
         for (Job* j : active) {
             if (j->P.precond == QXD_PRECOND_SAP && big(j)) {
-                if ((rc = sap_apply<float>(j->op, sap_single, j->phi[j->k], j->rin, j->P.sap_ncy, j->P.sap_nmr, st)))
-                    return rc;
+                same_op[{j->op, j->P.sap_ncy, j->P.sap_nmr}].push_back(j);
             } else if (j->P.precond == QXD_PRECOND_SAP) {
                 SapJob J{};
                 J.g = j->op->g;
@@ -344,6 +344,19 @@ struct Engine {
             } else {
                 QXD_CUDA(cudaMemcpyAsync(j->phi[j->k], j->rin, j->f32_bytes, cudaMemcpyDeviceToDevice, st));
             }
+        }
+        for (auto& kv : same_op) {
+            std::vector<void*> outs;
+            std::vector<const void*> ins;
+            std::vector<float4*> works;
+            for (Job* j : kv.second) {
+                outs.push_back(j->phi[j->k]);
+                ins.push_back(j->rin);
+                works.push_back((float4*)j->sapw);
+            }
+            if ((rc = sap_apply_multi(std::get<0>(kv.first), (int)outs.size(), outs.data(), ins.data(), works.data(),
+                                      std::get<1>(kv.first), std::get<2>(kv.first), st)))
+                return rc;
         }
         if (!sj.empty()) {
             if ((int)sj.size() > d_sap_cap) {

@@ -267,7 +267,9 @@ struct qxd_lattice {
     void* scratch_in = nullptr;   // native spinor FP64-sized
     void* scratch_out = nullptr;  // native spinor FP64-sized
     void* scratch_lex = nullptr;  // lexicographic FP64 spinor
-    float4* sap_r = nullptr;      // FP32 residual of the Schwarz method (first FP32 SAP application)
+    float4* sap_r = nullptr;      // FP32 work fields of the Schwarz method (delta, rho; first FP32 SAP application)
+    float4* sap_multi = nullptr;  // work fields of qxd_sap_multi, sap_multi_n right-hand sides
+    int sap_multi_n = 0;
     qxd::HostPipe* hostpipe = nullptr;  // streams and events of the pipelined host-buffer D
 
     qxd::SolverWork* solver = nullptr;  // Krylov work vectors (first solve)

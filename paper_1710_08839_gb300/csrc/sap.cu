@@ -617,23 +617,33 @@ enum SplitFlags : int {
     SF_KEEP_DELTA = 8,  // keep delta for the next visit of the other colour
 };
 
-// Work fields of the single-lattice FP32 solve: delta of every site
-// (6 float4 per site, stride V) and rho of the even sites (stride Vh)
+// One right-hand side of the FP32 block solve: source eta, output psi and the
+// work fields, delta of every site (6 float4 per site, stride V) and rho of
+// the even sites (stride Vh)
 struct SplitWork {
     const float4* eta;
+    float4* psi;
     float4* delta;
     float4* rho;
-    int flags;
+};
+
+// right-hand sides of one operator solved in one launch: each thread block
+// stages its block's links once and solves the block for each of them
+constexpr int SPLIT_MAXR = 12;
+struct SplitRhsList {
+    SplitWork r[SPLIT_MAXR];
+    int n;
 };
 
 // Same phases as sap_block_body, with the site-pair work split over the
-// two threads of a pair; the residual comes from eta on the first visit of
-// a colour, else from the kept rho and the crossing hops of the kept delta
-// (SplitWork).
+// two threads of a pair, for the right-hand sides rhs[0 .. nrhs) in turn
+// (the arithmetic of each is the same whatever the others); the residual
+// comes from eta on the first visit of a colour, else from the kept rho and
+// the crossing hops of the kept delta.
 template <bool QNZ>
 __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm, int bidx, int colour,
                                                const Fields<float>& f, const float4* __restrict__ Cinv,
-                                               const SplitWork& wk, int nmr, float q) {
+                                               const SplitWork* rhs, int nrhs, int flags, int nmr, float q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* sW4 = reinterpret_cast<float4*>(smem_raw);
     float2* sW2 = reinterpret_cast<float2*>(smem_raw + 16 * SPLIT_LINKS * sizeof(float4));
@@ -692,9 +702,12 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
         sW2[mu * SPLIT_LINKS + e] = make_float2(u[2][2].re, u[2][2].im);
     }
 
+#pragma unroll 1
+  for (int ir = 0; ir < nrhs; ++ir) {
+    const SplitWork& wk = rhs[ir];
     {
         cplx<float> r[12];
-        if (wk.flags & SF_FIRST) {
+        if (flags & SF_FIRST) {
             load_spinor(wk.eta, g.V, me.s, r);
         } else if (sg == 0) {  // even site: the kept rho
             load_spinor(wk.rho, g.Vh, me.s, r);
@@ -702,7 +715,7 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
 #pragma unroll
             for (int i = 0; i < 12; ++i) r[i] = mk(0.f, 0.f);
         }
-        if (wk.flags & SF_CROSS) {  // r -= D_cross delta = r + 1/2 (crossing hops of delta)
+        if (flags & SF_CROSS) {  // r -= D_cross delta = r + 1/2 (crossing hops of delta)
             cplx<float> acc[12];
 #pragma unroll
             for (int i = 0; i < 12; ++i) acc[i] = mk(0.f, 0.f);
@@ -775,7 +788,7 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
             }
             if (step == nsteps - 2) {
                 st_half(s_t, sg, t, de);  // delta_e for the last step
-                if (wk.flags & SF_KEEP_RHO) {
+                if (flags & SF_KEEP_RHO) {
                     // this thread's half of rho at the even site: components 3 sg + c and 6 + 3 sg + c
                     float2* kr = reinterpret_cast<float2*>(wk.rho);
 #pragma unroll
@@ -795,24 +808,28 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
     // psi_B += delta on this thread's site: delta_e in s_t, delta_o in s_rho
     cplx<float> d[12];
     ld_full(sg ? s_rho : s_t, t, d);
-    float4* psi = const_cast<float4*>(f.psi);
-    if (wk.flags & SF_KEEP_DELTA) store_spinor(wk.delta, g.V, me.s, d);
-    if (!(wk.flags & SF_FIRST)) {
+    if (flags & SF_KEEP_DELTA) store_spinor(wk.delta, g.V, me.s, d);
+    if (!(flags & SF_FIRST)) {
         cplx<float> o[12];
-        load_spinor(f.psi, g.V, me.s, o);
+        load_spinor(wk.psi, g.V, me.s, o);
 #pragma unroll
         for (int i = 0; i < 12; ++i) d[i] = d[i] + o[i];
     }
-    store_spinor(psi, g.V, me.s, d);
+    store_spinor(wk.psi, g.V, me.s, d);
+    if (ir + 1 < nrhs) __syncthreads();  // the next right-hand side reuses the block fields
+  }
 }
 
-template <bool QNZ>
+// MULTI: several right-hand sides per launch (else exactly one, and the
+// loop over them compiles away)
+template <bool QNZ, bool MULTI>
 __global__ void __launch_bounds__(SPLIT_THREADS, 2) k_sap_split(const __grid_constant__ Geom g,
                                                                 const __grid_constant__ SapGeom sgm, int colour,
                                                                 const __grid_constant__ Fields<float> f,
                                                                 const float4* __restrict__ Cinv,
-                                                                const __grid_constant__ SplitWork wk, int nmr, float q) {
-    sap_split_body<QNZ>(g, sgm, blockIdx.x, colour, f, Cinv, wk, nmr, q);
+                                                                const __grid_constant__ SplitRhsList rl, int flags,
+                                                                int nmr, float q) {
+    sap_split_body<QNZ>(g, sgm, blockIdx.x, colour, f, Cinv, rl.r, MULTI ? rl.n : 1, flags, nmr, q);
 }
 
 // batched form: thread block b works on block (b - cta_begin) of the job
@@ -827,8 +844,8 @@ __global__ void __launch_bounds__(SPLIT_THREADS, 2) k_sap_block_batch(const SapJ
         else hi = mid - 1;
     }
     const SapJob& J = jobs[lo];
-    const SplitWork wk{J.eta, J.delta, J.rho, flags};
-    sap_split_body<true>(J.g, J.sg, b - J.cta_begin, colour, J.f, J.Cinv, wk, nmr, J.q);
+    const SplitWork wk{J.eta, const_cast<float4*>(J.f.psi), J.delta, J.rho};
+    sap_split_body<true>(J.g, J.sg, b - J.cta_begin, colour, J.f, J.Cinv, &wk, 1, flags, nmr, J.q);
 }
 
 template <typename R>
@@ -865,41 +882,35 @@ int split_flags(int cy, int colour, int ncy) {
     return fl;
 }
 
-// visit `cy` of colour `colour` out of ncy cycles
-template <typename R, bool QNZ>
-int launch_sap_block(qxd_lattice* lat, const SapGeom& sg, int cy, int colour, int ncy, Fields<R> f,
-                     const typename Fields<R>::cvec* Cinv, const typename Fields<R>::vec* eta, int nmr,
-                     cudaStream_t st) {
-    const size_t smem = sap_smem_bytes<R>();
-    if constexpr (sizeof(R) == 4) {
-        const SplitWork wk{eta, lat->sap_r, lat->sap_r + (size_t)SPINOR_F4 * lat->g.V, split_flags(cy, colour, ncy)};
-        int rc = split_attrs(k_sap_split<QNZ>, smem);
-        if (rc) return rc;
-        k_sap_split<QNZ><<<sg.nhalf, SPLIT_THREADS, smem, st>>>(lat->g, sg, colour, f, Cinv, wk, nmr,
-                                                                (float)lat->qhat);
-        QXD_LAUNCHED("k_sap_split");
-    } else {
-        const int psi_zero = (cy == 0 && colour == 0) ? 1 : 0;
-        QXD_CUDA(cudaFuncSetAttribute(k_sap_block<R, QNZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_sap_block<R, QNZ><<<sg.nhalf, SAP_THREADS, smem, st>>>(lat->g, sg, colour, psi_zero, f, Cinv, eta, nmr,
-                                                                  (R)lat->qhat);
-        QXD_LAUNCHED("k_sap_block");
-    }
+// FP64 visit `cy` of colour `colour` out of ncy cycles
+template <bool QNZ>
+int launch_sap_block64(qxd_lattice* lat, const SapGeom& sg, int cy, int colour, Fields<double> f,
+                       const double* Cinv, const double2* eta, int nmr, cudaStream_t st) {
+    const size_t smem = sap_smem_bytes<double>();
+    const int psi_zero = (cy == 0 && colour == 0) ? 1 : 0;
+    QXD_CUDA(cudaFuncSetAttribute(k_sap_block<double, QNZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_sap_block<double, QNZ><<<sg.nhalf, SAP_THREADS, smem, st>>>(lat->g, sg, colour, psi_zero, f, Cinv, eta, nmr,
+                                                                   (double)lat->qhat);
+    QXD_LAUNCHED("k_sap_block");
     return QXD_OK;
 }
 
-template <typename R>
-Fields<R> sap_fields(qxd_lattice* lat, void* psi);
-template <>
-Fields<float> sap_fields<float>(qxd_lattice* lat, void* psi) {
-    return Fields<float>{(const float4*)psi, nullptr, lat->U32, lat->A32, lat->C32};
+// FP32: the ncy cycles for the right-hand sides of rl (one operator)
+template <bool QNZ, bool MULTI>
+int split_cycles(qxd_lattice* lat, const SapGeom& sg, const SplitRhsList& rl, int ncy, int nmr, cudaStream_t st) {
+    const size_t smem = sap_smem_bytes<float>();
+    int rc = split_attrs(k_sap_split<QNZ, MULTI>, smem);
+    if (rc) return rc;
+    const Fields<float> f{nullptr, nullptr, lat->U32, lat->A32, lat->C32};
+    for (int cy = 0; cy < ncy; ++cy)
+        for (int colour = 0; colour < 2; ++colour) {
+            k_sap_split<QNZ, MULTI><<<sg.nhalf, SPLIT_THREADS, smem, st>>>(lat->g, sg, colour, f, lat->Cinv32, rl,
+                                                                           split_flags(cy, colour, ncy), nmr,
+                                                                           (float)lat->qhat);
+            QXD_LAUNCHED("k_sap_split");
+        }
+    return QXD_OK;
 }
-template <>
-Fields<double> sap_fields<double>(qxd_lattice* lat, void* psi) {
-    return Fields<double>{(const double2*)psi, nullptr, lat->U64, lat->Zq64, lat->C64};
-}
-const float4* sap_cinv(qxd_lattice* lat, float) { return lat->Cinv32; }
-const double* sap_cinv(qxd_lattice* lat, double) { return lat->Cinv64; }
 
 }  // namespace
 
@@ -921,39 +932,60 @@ int sap_check(qxd_lattice* lat) {
     return QXD_OK;
 }
 
+int sap_apply_multi(qxd_lattice* lat, int nrhs, void* const* outs, const void* const* ins, float4* const* works,
+                    int ncy, int nmr, cudaStream_t st) {
+    const SapGeom sg = sap_geom(lat->g);
+    const size_t V = (size_t)lat->g.V;
+    for (int i0 = 0; i0 < nrhs; i0 += SPLIT_MAXR) {
+        SplitRhsList rl{};
+        rl.n = std::min(SPLIT_MAXR, nrhs - i0);
+        for (int i = 0; i < rl.n; ++i)
+            rl.r[i] = SplitWork{(const float4*)ins[i0 + i], (float4*)outs[i0 + i], works[i0 + i],
+                                works[i0 + i] + (size_t)SPINOR_F4 * V};
+        int rc;
+        if (rl.n > 1)
+            rc = lat->qhat != 0 ? split_cycles<true, true>(lat, sg, rl, ncy, nmr, st)
+                                : split_cycles<false, true>(lat, sg, rl, ncy, nmr, st);
+        else
+            rc = lat->qhat != 0 ? split_cycles<true, false>(lat, sg, rl, ncy, nmr, st)
+                                : split_cycles<false, false>(lat, sg, rl, ncy, nmr, st);
+        if (rc) return rc;
+    }
+    return QXD_OK;
+}
+
 template <typename R>
 int sap_apply(qxd_lattice* lat, SapWork& w, void* out, const void* in, int ncy, int nmr, cudaStream_t st) {
     const Geom& g = lat->g;
-    SapGeom& sg = w.sg;
-    sg.nb0 = g.N0 / SAP_BS;
-    sg.nb1 = g.N1 / SAP_BS;
-    sg.nb2 = g.N2 / SAP_BS;
-    sg.nb3 = g.N3 / SAP_BS;
-    sg.nblk = sg.nb0 * sg.nb1 * sg.nb2 * sg.nb3;
-    sg.nhalf = sg.nblk / 2;
-    Fields<R> f = sap_fields<R>(lat, out);
-    const typename Fields<R>::cvec* Cinv = sap_cinv(lat, R(0));
-    const typename Fields<R>::vec* eta = (const typename Fields<R>::vec*)in;
-    const bool qnz = lat->qhat != 0;
-    // FP64: psi starts at zero; the first half-cycle writes the blocks of
-    // colour 0 without reading psi, and the blocks of colour 1 must read zeros
-    // there. FP32: the first visit of each colour writes psi = delta.
-    if (sizeof(R) == 8) QXD_CUDA(cudaMemsetAsync(out, 0, (size_t)g.V * 24 * sizeof(R), st));
-    if (sizeof(R) == 4 && !lat->sap_r) {  // delta (V sites) and rho (Vh even sites)
-        const cudaError_t e = cudaMalloc(&lat->sap_r, ((size_t)g.V + g.Vh) * SPINOR_F4 * sizeof(float4));
-        if (e != cudaSuccess) {
-            lat->sap_r = nullptr;
-            return cuda_fail(e, "SAP: cudaMalloc(work fields)");
+    w.sg = sap_geom(g);
+    if constexpr (sizeof(R) == 4) {
+        // the first visit of each colour writes psi = delta; work fields: delta
+        // (V sites) and rho (Vh even sites), kept with the lattice
+        if (!lat->sap_r) {
+            const cudaError_t e = cudaMalloc(&lat->sap_r, ((size_t)g.V + g.Vh) * SPINOR_F4 * sizeof(float4));
+            if (e != cudaSuccess) {
+                lat->sap_r = nullptr;
+                return cuda_fail(e, "SAP: cudaMalloc(work fields)");
+            }
         }
+        float4* work = lat->sap_r;
+        return sap_apply_multi(lat, 1, &out, &in, &work, ncy, nmr, st);
+    } else {
+        // psi starts at zero; the first half-cycle writes the blocks of colour 0
+        // without reading psi, and the blocks of colour 1 must read zeros there
+        QXD_CUDA(cudaMemsetAsync(out, 0, (size_t)g.V * 24 * sizeof(R), st));
+        const Fields<double> f{(const double2*)out, nullptr, lat->U64, lat->Zq64, lat->C64};
+        for (int cy = 0; cy < ncy; ++cy)
+            for (int colour = 0; colour < 2; ++colour) {
+                const int rc = lat->qhat != 0
+                                   ? launch_sap_block64<true>(lat, w.sg, cy, colour, f, lat->Cinv64,
+                                                              (const double2*)in, nmr, st)
+                                   : launch_sap_block64<false>(lat, w.sg, cy, colour, f, lat->Cinv64,
+                                                               (const double2*)in, nmr, st);
+                if (rc) return rc;
+            }
+        return QXD_OK;
     }
-    int rc;
-    for (int cy = 0; cy < ncy; ++cy)
-        for (int colour = 0; colour < 2; ++colour) {
-            rc = qnz ? launch_sap_block<R, true>(lat, sg, cy, colour, ncy, f, Cinv, eta, nmr, st)
-                     : launch_sap_block<R, false>(lat, sg, cy, colour, ncy, f, Cinv, eta, nmr, st);
-            if (rc) return rc;
-        }
-    return QXD_OK;
 }
 
 template int sap_apply<float>(qxd_lattice*, SapWork&, void*, const void*, int, int, cudaStream_t);
@@ -1077,4 +1109,35 @@ extern "C" int qxd_sap(qxd_lattice* lat, void* out, const void* in, int ncy, int
                           : sap_apply<double>(lat, w, lat->scratch_out, lat->scratch_in, ncy, nmr, st);
     if (rc) return rc;
     return launch_unpack(lat, out, lat->scratch_out, prec, st);
+}
+
+extern "C" int qxd_sap_multi(qxd_lattice* lat, int nrhs, void* const* out, const void* const* in, int ncy, int nmr,
+                             void* stream) {
+    if (!lat || !out || !in || nrhs < 1) return fail(QXD_ERR_ARG, "qxd_sap_multi: NULL argument or nrhs < 1");
+    if (ncy < 1 || nmr < 1) return fail(QXD_ERR_ARG, "qxd_sap_multi: ncy and nmr must be >= 1");
+    for (int i = 0; i < nrhs; ++i) {
+        if (!out[i] || !in[i]) return fail(QXD_ERR_ARG, "qxd_sap_multi: NULL field");
+        for (int j = 0; j < nrhs; ++j)
+            if (out[i] == in[j] || (j != i && out[i] == out[j]))
+                return fail(QXD_ERR_ARG, "qxd_sap_multi: outputs must differ from each other and from the inputs");
+    }
+    if (!qxd::clover_ready(lat)) return fail(QXD_ERR_STATE, "qxd_sap_multi: needs qxd_sw_build first");
+    int rc = sap_check(lat);
+    if (rc) return rc;
+    const size_t per = ((size_t)lat->g.V + lat->g.Vh) * SPINOR_F4;  // float4 of one right-hand side's work fields
+    if (lat->sap_multi_n < nrhs) {
+        if (lat->sap_multi) cudaFree(lat->sap_multi);
+        lat->sap_multi = nullptr;
+        lat->sap_multi_n = 0;
+        const cudaError_t e = cudaMalloc(&lat->sap_multi, per * nrhs * sizeof(float4));
+        if (e != cudaSuccess) {
+            lat->sap_multi = nullptr;
+            return cuda_fail(e, "qxd_sap_multi: cudaMalloc(work fields)");
+        }
+        lat->sap_multi_n = nrhs;
+    }
+    std::vector<float4*> works(nrhs);
+    for (int i = 0; i < nrhs; ++i) works[i] = lat->sap_multi + per * i;
+    cudaStream_t st = stream ? (cudaStream_t)stream : lat->stream;
+    return sap_apply_multi(lat, nrhs, out, in, works.data(), ncy, nmr, st);
 }

@@ -85,6 +85,13 @@ int sap_check(qxd_lattice* lat);
 // black and white blocks, nmr minimal-residual steps per block solve
 template <typename R>
 int sap_apply(qxd_lattice* lat, SapWork& w, void* out, const void* in, int ncy, int nmr, cudaStream_t st);
+// outs[i] = SAP(ins[i]) in FP32 (native layout) for nrhs right-hand sides of
+// the operator lat, solved together (each thread block stages its block's
+// links once for all of them); works[i]: the work fields of right-hand side
+// i, (V + Vh) * 6 float4 (delta of every site, then rho of the even sites).
+// Each result is the same as with the right-hand side alone.
+int sap_apply_multi(qxd_lattice* lat, int nrhs, void* const* outs, const void* const* ins, float4* const* works,
+                    int ncy, int nmr, cudaStream_t st);
 
 int run_solve(qxd_lattice* lat, const qxd_solver_params& P, qxd_solve_info& info, cudaStream_t st);
 

@@ -106,6 +106,7 @@ SIGNATURES = {
     "qxd_eo_prepare": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_eo_reconstruct": (_i, [_vp, _vp, _vp, _i, _vp]),
     "qxd_sap": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
+    "qxd_sap_multi": (_i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _vp]),
     "qxd_solver_defaults": (None, [ctypes.POINTER(qxd_solver_params)]),
     "qxd_solve": (_i, [_vp, _vp, _vp, ctypes.POINTER(qxd_solver_params), ctypes.POINTER(qxd_solve_info), _vp]),
     "qxd_engine_create": (_i, [ctypes.POINTER(_vp), ctypes.c_size_t, _i, _vp]),
@@ -234,6 +235,13 @@ def qxd_eo_reconstruct(lat, x_ptr, b_ptr, flags, stream=0) -> int:
 
 def qxd_sap(lat, out_ptr, in_ptr, ncy, nmr, flags, stream=0) -> int:
     return check(_call("qxd_sap", lat, out_ptr, in_ptr, ncy, nmr, flags, stream))
+
+
+def qxd_sap_multi(lat, out_ptrs, in_ptrs, ncy, nmr, stream=0) -> int:
+    n = len(out_ptrs)
+    outs = (_vp * n)(*out_ptrs)
+    ins = (_vp * n)(*in_ptrs)
+    return check(_call("qxd_sap_multi", lat, n, outs, ins, ncy, nmr, stream))
 
 
 def qxd_solver_defaults() -> qxd_solver_params:
@@ -476,6 +484,14 @@ class Lattice:
         qxd_sap(self.handle, out.data_ptr(), inp.data_ptr(), ncy, nmr, flags, _stream_ptr(stream))
         return out
 
+
+    def sap_multi(self, outs, inps, ncy=5, nmr=5, stream=None):
+        """outs[i] = SAP(inps[i]) for several right-hand sides of this
+        operator in one pass (FP32 fields in the native layout, as from
+        pack(..., QXD_FP32))."""
+        qxd_sap_multi(self.handle, [o.data_ptr() for o in outs], [x.data_ptr() for x in inps], ncy, nmr,
+                      _stream_ptr(stream))
+        return outs
     def solve(self, x, b, stream=None, **kw):
         """Solve D x = b (FP64 complex128 tensors). Keyword arguments override
         the fields of qxd_solver_params. Returns (status, info dict)."""

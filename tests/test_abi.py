@@ -58,6 +58,7 @@ def test_null_arguments_are_errors():
     assert lib.qxd_Dw(None, None, None, 0, None) == qxd.QXD_ERR_ARG
     assert lib.qxd_set_params(None, 0.0, 0.0, 0.0, 0) == qxd.QXD_ERR_ARG
     assert lib.qxd_sw_build(None) == qxd.QXD_ERR_ARG
+    assert lib.qxd_sap_multi(None, 1, None, None, 5, 5, None) == qxd.QXD_ERR_ARG
     assert lib.qxd_lattice_destroy(None) == qxd.QXD_OK
     assert "NULL" in qxd.qxd_last_error() or qxd.qxd_last_error() != ""
 

@@ -391,3 +391,40 @@ def test_engine_large_lattice_path():
     assert float((x2 - xb).norm() / x2.norm()) < 1e-8
     lb.close()
     ls.close()
+
+
+def test_engine_same_operator_large_lattice():
+    """Requests on a lattice of 2^20 sites take the single-lattice Schwarz
+    kernels, and the requests of one operator are solved together (each
+    thread block stages its block's links once for all of them). Each result
+    equals the same request solved alone, bit for bit, and its residual with
+    the oracle's D at sampled sites (and the corners of the shifted
+    boundaries) stays at the tolerance."""
+    from paper_1710_08839_gb300 import qxd
+    c = Case(T=32, L1=16, L2=32, L3=32, qhat=2, m0=0.1, seed=9)
+    assert c.V == 1 << 20
+    lat = c.lattice()
+    rng = np.random.default_rng(29)
+    bs = [torch.from_numpy(rng.normal(size=(c.V, 4, 3)) + 1j * rng.normal(size=(c.V, 4, 3))).cuda()
+          for _ in range(3)]
+    eng = qxd.Engine(hbm_budget_bytes=64 << 30, max_active=16)
+    xs = [torch.zeros_like(b) for b in bs]
+    ids = [eng.submit(lat, x, b, tol=1e-10) for x, b in zip(xs, bs)]
+    eng.run()
+    for rid in ids:
+        done, info = eng.poll(rid)
+        assert done and info["status"] == qxd.QXD_OK and info["true_relres"] <= 1e-10, info
+    eng.close()
+    for x, b in zip(xs, bs):
+        assert torch.equal(_alone(lat, b), x)
+    lo = O.Lattice(c.T, c.L1, c.L2, c.L3, c.mask)
+    op = c.oracle()
+    idx = np.sort(rng.choice(c.V, size=400, replace=False))
+    corners = lo.index(np.array([[0, 0, 0, 0], [c.T - 1, c.N1 - 1, c.L2 - 1, c.L3 - 1],
+                                 [3, c.L1 - 1, 0, c.L3 - 1], [9, c.L1, c.L2 - 1, 0]]))
+    idx = np.unique(np.concatenate([idx, corners]))
+    for x, b in zip(xs, bs):
+        b_h = b.cpu().numpy()
+        r = b_h[idx] - op.apply_at(x.cpu().numpy(), idx)
+        assert np.linalg.norm(r) / np.linalg.norm(b_h[idx]) < 3e-10
+    lat.close()

@@ -101,3 +101,35 @@ def test_sap_rejects_incompatible_lattice():
         lat.sap(torch.empty_like(x), x)
     assert e.value.code == qxd.QXD_ERR_ARG
     lat.close()
+
+
+@pytest.mark.parametrize("name", ["cstar_8x16x8x8_q2", "cstar_8x16x8x8_q0"])
+def test_sap_multi_equals_sap_per_rhs(name):
+    """qxd_sap_multi (several right-hand sides per launch, links staged once
+    per block for all of them) gives each right-hand side the bits of
+    qxd_sap alone; the first is also checked against the oracle."""
+    from paper_1710_08839_gb300 import qxd
+    c = Case(**SAP_CASES[name])
+    lat = c.lattice()
+    rng = np.random.default_rng(17)
+    srcs = [c.psi] + [torch.from_numpy(rng.normal(size=(c.V, 4, 3)) + 1j * rng.normal(size=(c.V, 4, 3)))
+                      for _ in range(3)]
+    nb = lat.spinor_bytes(qxd.QXD_FP32)
+    ins, singles = [], []
+    for s_ in srcs:
+        xn = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        lat.pack(xn, s_.to(torch.complex64).cuda(), qxd.QXD_FP32)
+        ins.append(xn)
+        yn = torch.empty_like(xn)
+        lat.sap(yn, xn, 5, 5, native=True, prec=qxd.QXD_FP32)
+        singles.append(yn)
+    outs = [torch.empty_like(x) for x in ins]
+    lat.sap_multi(outs, ins, 5, 5)
+    torch.cuda.synchronize()
+    for o, s_ in zip(outs, singles):
+        assert torch.equal(o, s_)
+    y = torch.empty(c.V, 4, 3, dtype=torch.complex64, device="cuda")
+    lat.unpack(y, outs[0], qxd.QXD_FP32)
+    ref = O.sap(c.oracle(), c.psi.numpy(), 5, 5)
+    assert rel_norm(y.cpu().numpy().astype(np.complex128), ref) < 1e-5
+    lat.close()
