@@ -703,121 +703,121 @@ __device__ __forceinline__ void sap_split_body(const Geom& g, const SapGeom& sgm
     }
 
 #pragma unroll 1
-  for (int ir = 0; ir < nrhs; ++ir) {
-    const SplitWork& wk = rhs[ir];
-    {
-        cplx<float> r[12];
-        if (flags & SF_FIRST) {
-            load_spinor(wk.eta, g.V, me.s, r);
-        } else if (sg == 0) {  // even site: the kept rho
-            load_spinor(wk.rho, g.Vh, me.s, r);
-        } else {  // odd site: the block solve left no residual
+    for (int ir = 0; ir < nrhs; ++ir) {
+        const SplitWork& wk = rhs[ir];
+        {
+            cplx<float> r[12];
+            if (flags & SF_FIRST) {
+                load_spinor(wk.eta, g.V, me.s, r);
+            } else if (sg == 0) {  // even site: the kept rho
+                load_spinor(wk.rho, g.Vh, me.s, r);
+            } else {  // odd site: the block solve left no residual
 #pragma unroll
-            for (int i = 0; i < 12; ++i) r[i] = mk(0.f, 0.f);
-        }
-        if (flags & SF_CROSS) {  // r -= D_cross delta = r + 1/2 (crossing hops of delta)
-            cplx<float> acc[12];
-#pragma unroll
-            for (int i = 0; i < 12; ++i) acc[i] = mk(0.f, 0.f);
-            const int po = 1 - sg;  // parity of the neighbours
-            crossing_dir<QNZ, 0>(g, f, wk.delta, q, me, po, acc);
-            crossing_dir<QNZ, 1>(g, f, wk.delta, q, me, po, acc);
-            crossing_dir<QNZ, 2>(g, f, wk.delta, q, me, po, acc);
-            crossing_dir<QNZ, 3>(g, f, wk.delta, q, me, po, acc);
-#pragma unroll
-            for (int i = 0; i < 12; ++i) r[i] = r[i] + 0.5f * acc[i];
-        }
-        st_full(sg ? s_t : s_rho, t, r);
-    }
-    __syncthreads();
-
-    // r_o (this thread's half) stays in registers until the last step; the
-    // pair overwrites its own halves of s_t with t_o = M_oo^-1 r_o
-    cplx<float> ro[6], v[6], w[6], acc[6], rho[6];
-    ld_half(s_t, sg, t, ro);
-    clover_half(Cinv, g.V, so.s, sg, sgn, ro, w);
-    st_half(s_t, sg, t, w);
-    __syncthreads();
-
-    // rho stays in shared memory between steps (fewer live registers)
-    cplx<float> de[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) de[i] = mk(0.f, 0.f);
-    const int nsteps = 2 * nmr + 2;
-#pragma unroll 1
-    for (int step = 0; step < nsteps; ++step) {
-        const bool odd = (step & 1) != 0;
-        const bool last = step == nsteps - 1;
-        split_hops<QNZ>(bl, odd ? (last ? s_t : s_rho) : s_t, odd ? so : se, odd ? 1 : 0, sg, sgn, acc);
-        // acc = H psi on the sites of this step's parity (the links carry the -1/2)
-        if (step == 0) {
-            ld_half(s_rho, sg, t, rho);  // r_e
-#pragma unroll
-            for (int i = 0; i < 6; ++i) rho[i] = rho[i] - acc[i];
-            st_half(s_rho, sg, t, rho);
-        } else if (last) {
-#pragma unroll
-            for (int i = 0; i < 6; ++i) v[i] = ro[i] - acc[i];
-            clover_half(Cinv, g.V, so.s, sg, sgn, v, w);  // delta_o (s_rho is no longer read)
-            st_half(s_rho, sg, t, w);
-        } else if (odd) {
-            clover_half(Cinv, g.V, so.s, sg, sgn, acc, w);
-            st_half(s_t, sg, t, w);
-        } else {
-            ld_half(s_rho, sg, t, rho);
-            clover_half(f.C, g.V, se.s, sg, sgn, rho, w);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) w[i] = w[i] - acc[i];
-            float a_re = 0.f, a_im = 0.f, b = 0.f;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) {
-                a_re += w[i].re * rho[i].re + w[i].im * rho[i].im;
-                a_im += w[i].re * rho[i].im - w[i].im * rho[i].re;
-                b += w[i].re * w[i].re + w[i].im * w[i].im;
+                for (int i = 0; i < 12; ++i) r[i] = mk(0.f, 0.f);
             }
-            float sums[3];
-            // red is next written two steps later, after the barriers that end each step
-            block_sum3<float, SPLIT_THREADS, false>(a_re, a_im, b, red, sums);
-            if (sums[2] > 0.f) {  // else rho = 0 on the whole block: nothing to add
-                const cplx<float> om = mk(sums[0] / sums[2], sums[1] / sums[2]);
+            if (flags & SF_CROSS) {  // r -= D_cross delta = r + 1/2 (crossing hops of delta)
+                cplx<float> acc[12];
 #pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    de[i] = de[i] + om * rho[i];
-                    rho[i] = rho[i] - om * w[i];
-                }
+                for (int i = 0; i < 12; ++i) acc[i] = mk(0.f, 0.f);
+                const int po = 1 - sg;  // parity of the neighbours
+                crossing_dir<QNZ, 0>(g, f, wk.delta, q, me, po, acc);
+                crossing_dir<QNZ, 1>(g, f, wk.delta, q, me, po, acc);
+                crossing_dir<QNZ, 2>(g, f, wk.delta, q, me, po, acc);
+                crossing_dir<QNZ, 3>(g, f, wk.delta, q, me, po, acc);
+#pragma unroll
+                for (int i = 0; i < 12; ++i) r[i] = r[i] + 0.5f * acc[i];
             }
-            if (step == nsteps - 2) {
-                st_half(s_t, sg, t, de);  // delta_e for the last step
-                if (flags & SF_KEEP_RHO) {
-                    // this thread's half of rho at the even site: components 3 sg + c and 6 + 3 sg + c
-                    float2* kr = reinterpret_cast<float2*>(wk.rho);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const int i = 6 * h + 3 * sg + c;
-                            kr[2 * ((size_t)(i >> 1) * g.Vh + se.s) + (i & 1)] = make_float2(rho[3 * h + c].re, rho[3 * h + c].im);
-                        }
-                }
-            } else {
-                st_half(s_rho, sg, t, rho);
-            }
+            st_full(sg ? s_t : s_rho, t, r);
         }
         __syncthreads();
-    }
-    // psi_B += delta on this thread's site: delta_e in s_t, delta_o in s_rho
-    cplx<float> d[12];
-    ld_full(sg ? s_rho : s_t, t, d);
-    if (flags & SF_KEEP_DELTA) store_spinor(wk.delta, g.V, me.s, d);
-    if (!(flags & SF_FIRST)) {
-        cplx<float> o[12];
-        load_spinor(wk.psi, g.V, me.s, o);
+
+        // r_o (this thread's half) stays in registers until the last step; the
+        // pair overwrites its own halves of s_t with t_o = M_oo^-1 r_o
+        cplx<float> ro[6], v[6], w[6], acc[6], rho[6];
+        ld_half(s_t, sg, t, ro);
+        clover_half(Cinv, g.V, so.s, sg, sgn, ro, w);
+        st_half(s_t, sg, t, w);
+        __syncthreads();
+
+        // rho stays in shared memory between steps (fewer live registers)
+        cplx<float> de[6];
 #pragma unroll
-        for (int i = 0; i < 12; ++i) d[i] = d[i] + o[i];
+        for (int i = 0; i < 6; ++i) de[i] = mk(0.f, 0.f);
+        const int nsteps = 2 * nmr + 2;
+#pragma unroll 1
+        for (int step = 0; step < nsteps; ++step) {
+            const bool odd = (step & 1) != 0;
+            const bool last = step == nsteps - 1;
+            split_hops<QNZ>(bl, odd ? (last ? s_t : s_rho) : s_t, odd ? so : se, odd ? 1 : 0, sg, sgn, acc);
+            // acc = H psi on the sites of this step's parity (the links carry the -1/2)
+            if (step == 0) {
+                ld_half(s_rho, sg, t, rho);  // r_e
+#pragma unroll
+                for (int i = 0; i < 6; ++i) rho[i] = rho[i] - acc[i];
+                st_half(s_rho, sg, t, rho);
+            } else if (last) {
+#pragma unroll
+                for (int i = 0; i < 6; ++i) v[i] = ro[i] - acc[i];
+                clover_half(Cinv, g.V, so.s, sg, sgn, v, w);  // delta_o (s_rho is no longer read)
+                st_half(s_rho, sg, t, w);
+            } else if (odd) {
+                clover_half(Cinv, g.V, so.s, sg, sgn, acc, w);
+                st_half(s_t, sg, t, w);
+            } else {
+                ld_half(s_rho, sg, t, rho);
+                clover_half(f.C, g.V, se.s, sg, sgn, rho, w);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) w[i] = w[i] - acc[i];
+                float a_re = 0.f, a_im = 0.f, b = 0.f;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    a_re += w[i].re * rho[i].re + w[i].im * rho[i].im;
+                    a_im += w[i].re * rho[i].im - w[i].im * rho[i].re;
+                    b += w[i].re * w[i].re + w[i].im * w[i].im;
+                }
+                float sums[3];
+                // red is next written two steps later, after the barriers that end each step
+                block_sum3<float, SPLIT_THREADS, false>(a_re, a_im, b, red, sums);
+                if (sums[2] > 0.f) {  // else rho = 0 on the whole block: nothing to add
+                    const cplx<float> om = mk(sums[0] / sums[2], sums[1] / sums[2]);
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        de[i] = de[i] + om * rho[i];
+                        rho[i] = rho[i] - om * w[i];
+                    }
+                }
+                if (step == nsteps - 2) {
+                    st_half(s_t, sg, t, de);  // delta_e for the last step
+                    if (flags & SF_KEEP_RHO) {
+                        // this thread's half of rho at the even site: components 3 sg + c and 6 + 3 sg + c
+                        float2* kr = reinterpret_cast<float2*>(wk.rho);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                const int i = 6 * h + 3 * sg + c;
+                                kr[2 * ((size_t)(i >> 1) * g.Vh + se.s) + (i & 1)] = make_float2(rho[3 * h + c].re, rho[3 * h + c].im);
+                            }
+                    }
+                } else {
+                    st_half(s_rho, sg, t, rho);
+                }
+            }
+            __syncthreads();
+        }
+        // psi_B += delta on this thread's site: delta_e in s_t, delta_o in s_rho
+        cplx<float> d[12];
+        ld_full(sg ? s_rho : s_t, t, d);
+        if (flags & SF_KEEP_DELTA) store_spinor(wk.delta, g.V, me.s, d);
+        if (!(flags & SF_FIRST)) {
+            cplx<float> o[12];
+            load_spinor(wk.psi, g.V, me.s, o);
+#pragma unroll
+            for (int i = 0; i < 12; ++i) d[i] = d[i] + o[i];
+        }
+        store_spinor(wk.psi, g.V, me.s, d);
+        if (ir + 1 < nrhs) __syncthreads();  // the next right-hand side reuses the block fields
     }
-    store_spinor(wk.psi, g.V, me.s, d);
-    if (ir + 1 < nrhs) __syncthreads();  // the next right-hand side reuses the block fields
-  }
 }
 
 // MULTI: several right-hand sides per launch (else exactly one, and the
