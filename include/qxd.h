@@ -21,7 +21,11 @@
  *    given at create time). Calls are asynchronous on that stream unless
  *    stated otherwise; calls that return a device-side status (set_gauge,
  *    sw_build, solve) synchronise that stream.
- *  - Threads: one lattice must not be used by two host threads at once.
+ *  - Threads: one lattice must not be used by two host threads at once, nor
+ *    by calls on two streams whose work may overlap on the GPU: a lattice's
+ *    calls share its conversion scratch and work fields (Schwarz, solver,
+ *    deflation). The engine and server keep the work fields of every request
+ *    apart, so their requests may share an operator.
  *  - Site order ("lexicographic"): x = (x0, x1, x2, x3) over the simulated
  *    lattice N = (T, N1, L2, L3), N1 = 2 L1 when direction 1 is C*, else L1;
  *    index ((x0 N1 + x1) L2 + x2) L3 + x3 (x3 fastest).
