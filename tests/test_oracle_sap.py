@@ -207,3 +207,71 @@ def test_planted_mr_mistakes_are_caught(name):
     ns = dict(vars(O.qxd_oracle))
     exec(compile(src.replace(old, new), "<planted block_mr>", "exec"), ns)
     assert not mr_pins_hold(ns["block_mr"]), name
+
+
+def sap_carried(op, eta, ncy, nmr, bs, cross_sign=1.0):
+    """The Schwarz sweep of oracle.sap with the residual of a block visit
+    carried instead of recomputed: the even-odd block solve leaves the block
+    residual r_B - D_B delta_B equal to the MR residual rho on the even sites
+    and to zero on the odd ones (the odd rows are solved exactly), and
+    between two visits of a colour psi changes only by the other colour's
+    last correction, whose D reaches the blocks of this colour only through
+    the hops crossing their faces. So a visit starts from eta (first visit)
+    or the kept rho, minus D of the other colour's last correction there.
+    cross_sign plants a sign mistake in that term."""
+    lat = op.lat
+    V = lat.V
+    c = lat.coords(lat.all_sites())
+    B = c // bs
+    nb = [lat.N[mu] // bs for mu in range(4)]
+    block_id = ((B[:, 0] * nb[1] + B[:, 1]) * nb[2] + B[:, 2]) * nb[3] + B[:, 3]
+    colour = B.sum(axis=1) % 2
+    parity = c.sum(axis=1) % 2
+    eo = O.EvenOdd(op)
+    inv_full = np.zeros((V, 12, 12), dtype=np.complex128)
+    inv_full[eo.odd] = np.linalg.inv(eo.Doo_blocks)
+
+    def restrict(f, mask):
+        g = np.zeros_like(f)
+        g[mask] = f[mask]
+        return g
+
+    psi = np.zeros_like(eta)
+    kept = [None, None]
+    last = [np.zeros_like(eta), np.zeros_like(eta)]   # each colour's last correction
+    for cy in range(ncy):
+        for col in (0, 1):
+            inb = colour == col
+            even_b, odd_b = inb & (parity == 0), inb & (parity == 1)
+
+            def D_B_eo(f, rows, cols):
+                return restrict(restrict(op.apply(restrict(restrict(f, cols), inb)), inb), rows)
+
+            def Doo_inv_B(f):
+                return restrict(np.einsum("nij,nj->ni", inv_full, f.reshape(V, 12)).reshape(V, 4, 3), odd_b)
+
+            def D_hat_B(f):
+                return D_B_eo(f, even_b, even_b) - D_B_eo(Doo_inv_B(D_B_eo(f, odd_b, even_b)), even_b, odd_b)
+
+            base = restrict(eta, inb) if cy == 0 else kept[col]
+            r = base - cross_sign * restrict(op.apply(last[1 - col]), inb)
+            ce = restrict(r, even_b) - D_B_eo(Doo_inv_B(r), even_b, odd_b)
+            y, rho = O.block_mr(D_hat_B, ce, block_id, int(np.prod(nb)), nmr, even_b)
+            yo = Doo_inv_B(restrict(r, odd_b) - D_B_eo(y, odd_b, even_b))
+            last[col] = y + yo
+            kept[col] = rho
+            psi = psi + y + yo
+    return psi
+
+
+def test_carried_residual_equals_recomputed_residual():
+    """The identity behind the FP32 Schwarz kernel, which carries the
+    residual of a block visit from the previous visits instead of computing
+    eta - D psi: with the same sweep the two agree to rounding, and the
+    check is sharp (the crossing term with the wrong sign fails it)."""
+    _, op, eta = setup()
+    ref = O.sap(op, eta, 3, 3, bs=BS)
+    got = sap_carried(op, eta, 3, 3, BS)
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-12
+    bad = sap_carried(op, eta, 3, 3, BS, cross_sign=-1.0)
+    assert np.abs(bad - ref).max() / np.abs(ref).max() > 1e-3
