@@ -104,3 +104,35 @@ def pin_preconditioner_exact_on_DS(lat=O.Lattice(4, 4, 4, 4, 0b1110), seed=44):
     A = DF.little_operator(op, phi, BS)
     got = DF.deflated_preconditioner(op, phi, A, op.apply(x), 2, 2, BS)
     return np.abs(got - x).max() / np.abs(x).max()
+
+
+def pin_little_even_odd(lat=O.Lattice(4, 4, 4, 4, 0b1110), seed=45, planted_colouring=False):
+    """The structure the GPU's even-odd little solve relies on: neighbouring
+    blocks have opposite colours (parity of the block coordinates, also
+    across the shifted C* boundary), so A couples no two different blocks of
+    one colour; hence A_oo is block diagonal and A y = c is solved by
+    y_e = (A_ee - A_eo A_oo^-1 A_oe)^-1 (c_e - A_eo A_oo^-1 c_o),
+    y_o = A_oo^-1 (c_o - A_oe y_e). Returns the larger of the same-colour
+    coupling (relative to max |A|) and the relative error of that solve
+    against the dense solve. planted_colouring colours the blocks by B3 alone
+    (a plausible mistake), which leaves same-colour couplings."""
+    r, op, phi = _random_case(lat, seed)
+    ns = phi.shape[0]
+    nblk = DF.block_index(lat, BS).max() + 1
+    nb = [lat.N[mu] // BS for mu in range(4)]
+    B = np.array(np.unravel_index(np.arange(nblk), nb))
+    colour = (B[3] if planted_colouring else B.sum(axis=0)) % 2
+    A = DF.little_operator(op, phi, BS)
+    A4 = A.reshape(nblk, ns, nblk, ns)
+    same = (colour[:, None] == colour[None, :]) & ~np.eye(nblk, dtype=bool)
+    off = np.abs(A4.transpose(0, 2, 1, 3)[same]).max() / np.abs(A).max()
+    ie = np.nonzero(np.repeat(colour == 0, ns))[0]
+    io = np.nonzero(np.repeat(colour == 1, ns))[0]
+    c = r.normal(size=nblk * ns) + 1j * r.normal(size=nblk * ns)
+    Aee, Aeo, Aoe, Aoo = A[np.ix_(ie, ie)], A[np.ix_(ie, io)], A[np.ix_(io, ie)], A[np.ix_(io, io)]
+    schur = Aee - Aeo @ np.linalg.solve(Aoo, Aoe)
+    y = np.zeros_like(c)
+    y[ie] = np.linalg.solve(schur, c[ie] - Aeo @ np.linalg.solve(Aoo, c[io]))
+    y[io] = np.linalg.solve(Aoo, c[io] - Aoe @ y[ie])
+    ref = np.linalg.solve(A, c)
+    return max(off, np.abs(y - ref).max() / np.abs(ref).max())

@@ -23,6 +23,11 @@ def test_deflated_preconditioner_exact_on_the_deflation_image():
     assert PD.pin_preconditioner_exact_on_DS() < 1e-10
 
 
+def test_little_system_splits_by_block_colour():
+    assert PD.pin_little_even_odd() < 1e-10
+    assert PD.pin_little_even_odd(planted_colouring=True) > 1e-3
+
+
 _ORIG_LITTLE = DF.little_operator
 _ORIG_ORTH = DF.block_orthonormalize
 _ORIG_PRE = DF.deflated_preconditioner
