@@ -20,6 +20,7 @@ the bytes of all ranks over the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import hashlib
 import json
 import os
@@ -223,6 +224,51 @@ def write_traffic_record(csv_path):
     return rec
 
 
+# --kernel-times: device time per kernel of selected regions (torch.profiler,
+# CUPTI activity records of every kernel on the device, the library's
+# included); timings taken under it carry the profiler's overhead
+KERNEL_TIMES = {"on": False}
+
+
+@contextlib.contextmanager
+def kernel_times(out, top=16):
+    if not KERNEL_TIMES["on"]:
+        yield
+        return
+    import re
+    import torch
+    from torch.profiler import profile, ProfilerActivity
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        yield
+        torch.cuda.synchronize()
+    tot = {}
+    for e in prof.events():
+        if e.device_type != torch.autograd.DeviceType.CUDA:
+            continue
+        m = re.search(r"(k_\w+)(<[^(]*>)?", e.name)
+        k = (m.group(1) + (m.group(2) or "")) if m else e.name[:48]
+        t = tot.setdefault(k, [0, 0.0])
+        t[0] += 1
+        t[1] += getattr(e, "device_time_total", 0.0) or getattr(e, "cuda_time_total", 0.0)
+    busy = sum(v[1] for v in tot.values())
+    rows = sorted(tot.items(), key=lambda kv: -kv[1][1])[:top]
+    out["kernel_times"] = {"device_ms": busy / 1e3,
+                           "kernels": [{"kernel": k, "launches": n, "ms": us / 1e3,
+                                        "share": us / busy if busy else 0.0} for k, (n, us) in rows]}
+
+
+def _start_kernel_times():
+    """The first profiler session of a process records no device activity:
+    open and close one before the measured regions."""
+    KERNEL_TIMES["on"] = True
+    import torch
+    from torch.profiler import profile, ProfilerActivity
+    with profile(activities=[ProfilerActivity.CUDA]):
+        torch.zeros(1, device="cuda").add_(1)
+        torch.cuda.synchronize()
+
+
 def make_inputs(device, w=None):
     import synth
     w = w or WORKLOAD
@@ -373,12 +419,14 @@ def batch_benchmark(qxd, torch):
     # second is timed
     eng = qxd.Engine(hbm_budget_bytes=w["budget_gb"] << 30, max_active=nreq)
     xs = [torch.zeros_like(b) for _, b in reqs]
+    kt_eng = {}
     for timed in (False, True):
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ids = [eng.submit(v, x, b, tol=w["tol"]) for (v, b), x in zip(reqs, xs)]
-        eng.run()
-        t_eng = time.perf_counter() - t0
+        with kernel_times(kt_eng) if timed else contextlib.nullcontext():
+            t0 = time.perf_counter()
+            ids = [eng.submit(v, x, b, tol=w["tol"]) for (v, b), x in zip(reqs, xs)]
+            eng.run()
+            t_eng = time.perf_counter() - t0
         infos = [eng.poll(i)[1] for i in ids]
         for i in ids:
             eng.forget(i)
@@ -411,7 +459,7 @@ def batch_benchmark(qxd, torch):
                     "(4^4, ncy 5, nmr 5) in lockstep, batched launches",
         "requests": nreq, "all_converged": ok,
         "max_true_relres": max(i["true_relres"] for i in infos),
-        "engine_s": t_eng, "engine_solves_per_s": nreq / t_eng, "engine_steps": stats["steps"],
+        "engine_s": t_eng, "engine_solves_per_s": nreq / t_eng, "engine_steps": stats["steps"], **kt_eng,
         "sequential_fp64_s_est": seq64, "sequential_fp64_solves_per_s_est": nreq / seq64,
         "sequential_mixed_s_est": seqmix,
         "speedup_vs_sequential_fp64": seq64 / t_eng, "speedup_vs_sequential_mixed": seqmix / t_eng,
@@ -790,10 +838,13 @@ def dfl_benchmark(qxd, torch):
     x = torch.zeros_like(b)
     lat.solve(x, b, tol=D["tol"], precond=qxd.QXD_PRECOND_SAP, inner_prec=qxd.QXD_FP32)  # warm-up
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rc, info = lat.solve(x, b, tol=D["tol"], precond=qxd.QXD_PRECOND_SAP, inner_prec=qxd.QXD_FP32)
-    out["sap"] = {"status": rc, "s": time.perf_counter() - t0, "iterations": info["iterations"],
-                  "true_relres": info["true_relres"]}
+    kt_sap = {}
+    with kernel_times(kt_sap):
+        t0 = time.perf_counter()
+        rc, info = lat.solve(x, b, tol=D["tol"], precond=qxd.QXD_PRECOND_SAP, inner_prec=qxd.QXD_FP32)
+        t_sap = time.perf_counter() - t0
+    out["sap"] = {"status": rc, "s": t_sap, "iterations": info["iterations"],
+                  "true_relres": info["true_relres"], **kt_sap}
     t0 = time.perf_counter()
     lat.dfl_subspace(D["ns"], niter=D["niter"], ncy=D["ncy"], seed=D["seed"])
     out["subspace_build_s"] = time.perf_counter() - t0
@@ -801,11 +852,14 @@ def dfl_benchmark(qxd, torch):
     lat.dfl_refresh()
     out["little_operator_s"] = time.perf_counter() - t0
     x2 = torch.zeros_like(b)
-    t0 = time.perf_counter()
-    rc, info = lat.solve(x2, b, tol=D["tol"], precond=qxd.QXD_PRECOND_DFL_SAP, inner_prec=qxd.QXD_FP32)
-    out["dfl_sap"] = {"status": rc, "s": time.perf_counter() - t0, "iterations": info["iterations"],
+    kt_dfl = {}
+    with kernel_times(kt_dfl):
+        t0 = time.perf_counter()
+        rc, info = lat.solve(x2, b, tol=D["tol"], precond=qxd.QXD_PRECOND_DFL_SAP, inner_prec=qxd.QXD_FP32)
+        t_dfl = time.perf_counter() - t0
+    out["dfl_sap"] = {"status": rc, "s": t_dfl, "iterations": info["iterations"],
                       "little_iters": info["little_iters"], "true_relres": info["true_relres"],
-                      "rel_diff_vs_sap": float((x2 - x).norm() / x.norm())}
+                      "rel_diff_vs_sap": float((x2 - x).norm() / x.norm()), **kt_dfl}
     lat.close()
     return out
 
@@ -1125,6 +1179,9 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the multi-RHS summary of the default line")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving summary of the default line")
+    ap.add_argument("--kernel-times", action="store_true",
+                    help="with --mode dfl or batch: device time per kernel of the timed solves (torch.profiler; "
+                         "the timings then include its overhead)")
     ap.add_argument("--write-traffic", metavar="NCU_CSV",
                     help="write profiles/dirac_fp32_q2_traffic.json from an ncu CSV of k_dirac launches and exit")
     args = ap.parse_args()
@@ -1148,6 +1205,8 @@ def main():
     from paper_1710_08839_gb300 import qxd
 
     if args.mode in ("solve", "sap", "batch", "serve", "rational", "flow", "dfl", "alu", "oracle"):
+        if args.kernel_times:
+            _start_kernel_times()
         if args.mode == "oracle":
             res = oracle_benchmark(qxd, torch)
         elif args.mode == "alu":
